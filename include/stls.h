@@ -1,0 +1,165 @@
+/*
+ * stls.h -- C ABI of the GB300 space-time least-squares heat-equation solver.
+ *
+ * Problem (Montardini, Negri, Sangalli, Tani, arXiv:1809.10026):
+ *   heat equation d_t u - Lap u = f on (0,1)^d x (0,T), u = 0 on the spatial
+ *   boundary, u = 0 at t = 0 (Sec. 3.1, Eq. heat_eq), discretized by the
+ *   least-squares method of Sec. 3.3 with tensor-product B-splines of degree
+ *   p_s in space and p_t in time on uniform open knot vectors (Sec. 2).
+ *   The unknowns are the coefficients of the reduced basis of Sec. 2.2: space
+ *   directions drop their first and last B-spline, time drops its first one,
+ *   so n_s,k = n_el,k + p_s - 2, n_t = n_el,t + p_t - 1, N = n_t * prod n_s,k.
+ *
+ * Layout of every vector argument: FP64, colexicographic order of Sec. 4
+ *   (Eq. kron_vec_multi): direction 1 fastest, time slowest; a batch of B
+ *   right-hand sides is B consecutive vectors of N entries (row-major
+ *   (B, n_t, n_d, ..., n_1)).  Device pointers must be 8-byte aligned and may
+ *   not overlap unless a function says otherwise.
+ *
+ * Ownership: the caller owns every buffer it passes in; the context owns its
+ *   1D factors and its workspace, allocated once in stls_create.  No call
+ *   other than stls_create allocates device memory.
+ *
+ * Streams: every call is ordered on the CUDA stream given to stls_create or
+ *   stls_set_stream.  stls_apply_* are asynchronous; stls_solve* synchronize
+ *   with the host to test convergence.
+ *
+ * Errors: every int-returning call returns STLS_OK (0) or a stls_status code,
+ *   and stls_last_error(ctx) describes the last failure.  Invalid sizes or
+ *   parameters are rejected before any launch.
+ */
+#ifndef STLS_H
+#define STLS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct stls_ctx stls_ctx;
+
+enum stls_status {
+  STLS_OK = 0,
+  STLS_EINVAL = 1,      /* invalid parameter, size or pointer */
+  STLS_ENOMEM = 2,      /* device or host allocation failed (stls_create only) */
+  STLS_ECUDA = 3,       /* a CUDA runtime call or kernel launch failed */
+  STLS_ENOTCONV = 4,    /* CG reached maxit before the tolerance */
+  STLS_EBREAKDOWN = 5,  /* CG breakdown: (p, A p) <= 0 or (z, r) <= 0 */
+  STLS_ENONFINITE = 6   /* a NaN or Inf appeared in the data or the iteration */
+};
+
+/* Arithmetic of the preconditioner's mode products (Algorithm 1, steps 2 and 4).
+ * STLS_FP64: FP64 throughout.  STLS_MIXED_TF32 / STLS_MIXED_BF16: the mode
+ * products run on the tensor cores with TF32 / BF16 operands and FP32
+ * accumulation; the eigenvalue division, A x, the CG vectors and inner
+ * products stay FP64.  The mixed forms should be used with flexible = 1. */
+enum stls_precision { STLS_FP64 = 0, STLS_MIXED_TF32 = 1, STLS_MIXED_BF16 = 2 };
+
+typedef struct {
+  int d;            /* spatial dimension, 1..3 */
+  int p_s;          /* spline degree in space, >= 2 (C^1 splines, Assumption 2) */
+  int p_t;          /* spline degree in time, >= 1 */
+  int n_el_s[3];    /* elements per spatial direction (first d entries), >= 1 */
+  int n_el_t;       /* elements in time, >= 1 */
+  double T;         /* final time, > 0 */
+  int precision;    /* enum stls_precision */
+  int flexible;     /* 1: flexible CG (Polak-Ribiere beta), 0: standard PCG */
+  int batch;        /* right-hand sides per call, 1..1024 */
+  int time_pencil;  /* 0: time pencil (M_t, K_t) on [0,T]; 1: parametric (T = 1)
+                       pencil of Eq. preconditioner.  Equal when T = 1. */
+} stls_params;
+
+typedef struct {
+  int iters;            /* CG iterations performed */
+  int status;           /* STLS_OK, STLS_ENOTCONV, STLS_EBREAKDOWN or STLS_ENONFINITE */
+  double rel_res;       /* ||r_k|| / ||F|| of the recursively updated residual */
+  double true_rel_res;  /* ||F - A u|| / ||F|| recomputed in FP64 at exit */
+} stls_solve_info;
+
+/* Create a solver context: builds the 1D Galerkin matrices (Sec. 4.1-4.2) and
+ * the generalized eigendecompositions of Algorithm 1, step 1, on the host in
+ * FP64, uploads them and allocates the workspace for `batch` right-hand
+ * sides.  `cuda_stream` is a cudaStream_t (NULL = legacy default stream).
+ * On failure *out is NULL and the return code says why. */
+int stls_create(stls_ctx **out, const stls_params *prm, void *cuda_stream);
+
+/* Release everything the context owns.  NULL is accepted. */
+void stls_destroy(stls_ctx *ctx);
+
+/* Text of the last error on this context ("" if none).  With ctx == NULL,
+ * the last stls_create failure of the calling thread. */
+const char *stls_last_error(const stls_ctx *ctx);
+
+/* Change the stream used by later calls. */
+int stls_set_stream(stls_ctx *ctx, void *cuda_stream);
+
+/* Sizes: n_s[0..d-1] reduced spatial sizes, *n_t, *n_dof = N (per RHS),
+ * *batch.  Any pointer may be NULL. */
+int stls_sizes(const stls_ctx *ctx, int *n_s, int *n_t, long long *n_dof, int *batch);
+
+/* y = A x for the batch (Eq. A_kron: A = K_t x M_s + M_t x J_s + W_t x L_s),
+ * matrix-free by banded mode products in FP64.  x, y: device, B x N. */
+int stls_apply_A(stls_ctx *ctx, const double *x, double *y);
+
+/* z = P^{-1} r for the batch by fast diagonalization (Eq. preconditioner,
+ * Algorithm 1, steps 2-4) in the context's precision.  r, z: device, B x N;
+ * r == z is allowed. */
+int stls_apply_precond(stls_ctx *ctx, const double *r, double *z);
+
+/* Solve A u = F for the batch by (flexible) preconditioned CG from u = 0,
+ * stopping each right-hand side when ||r_k|| / ||F|| <= tol (Sec. 5: tolerance
+ * on the relative residual, zero initial guess).  F, u: device, B x N.
+ * info: host array of B entries (may be NULL).  Returns STLS_OK if every
+ * right-hand side converged, else the first non-OK per-RHS status. */
+int stls_solve(stls_ctx *ctx, const double *F, double *u, double tol, int maxit,
+               stls_solve_info *info);
+
+/* As stls_solve, with F and u in HOST memory (B x N each): copies F to the
+ * device, solves, copies u back, all on the context's stream.  Pinned host
+ * memory gives the fastest copies. */
+int stls_solve_host(stls_ctx *ctx, const double *F_host, double *u_host, double tol,
+                    int maxit, stls_solve_info *info);
+
+/* Lifting of a non-zero initial datum u0 = sum_i c0_i B_i(x) (Sec. 3.1):
+ * y = G c0 with G = e_T x L_s + m_t x J_s, where e_T holds the time basis at
+ * t = T and m_t its integrals over (0,T).  The discrete problem with initial
+ * datum u0 is A w = F - G c0, and u = w + 1_{n_t} x c0.
+ * c0: device, B x N_s; y: device, B x N. */
+int stls_apply_lift(stls_ctx *ctx, const double *c0, double *y);
+
+/* Adjoint of the lifted solve for a loss L(u): given g = dL/du and
+ * lam = A^{-1} g, writes dc0 = sum_t g[t, :] - G^T lam (device, B x N_s). */
+int stls_lift_adjoint(stls_ctx *ctx, const double *g, const double *lam, double *dc0);
+
+/* Factor ids for stls_get_factor / stls_host_factor. */
+enum stls_factor {
+  STLS_F_MASS = 0,      /* n x n  M_k (space) / M_t (time, on [0,T]) */
+  STLS_F_STIFF = 1,     /* n x n  K_k / K_t */
+  STLS_F_BILAP = 2,     /* n x n  J_k = int b''_i b''_j (space only) */
+  STLS_F_EIGVEC = 3,    /* n x n  U of the preconditioner pencil, row-major */
+  STLS_F_EIGVAL = 4,    /* n      Lambda of the preconditioner pencil, ascending */
+  STLS_F_END = 5,       /* n      time basis at t = T (time only) */
+  STLS_F_INTEGRAL = 6   /* n      integrals of the reduced basis functions */
+};
+
+/* Copy a 1D factor of direction `dir` (0..d-1 space, d = time) to host
+ * memory.  Matrices are row-major. */
+int stls_get_factor(const stls_ctx *ctx, int which, int dir, double *host_out);
+
+/* Same as stls_get_factor but computed on the host from `prm` alone, without
+ * a GPU or a context.  Returns STLS_EINVAL for invalid parameters. */
+int stls_host_factor(const stls_params *prm, int which, int dir, double *host_out);
+
+/* Number of kernels this context has launched since creation. */
+long long stls_launch_count(const stls_ctx *ctx);
+
+/* Per-phase device timing of solves.  When enabled, stls_solve records CUDA
+ * events around each phase; stls_phase_times returns, for phase ids
+ * 0 = A x, 1 = P^{-1} r, 2 = CG vector updates and reductions, the summed
+ * milliseconds and the number of executions since the last reset. */
+int stls_enable_timing(stls_ctx *ctx, int on);
+int stls_phase_times(stls_ctx *ctx, double *ms_out3, long long *count_out3);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STLS_H */

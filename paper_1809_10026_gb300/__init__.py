@@ -1,0 +1,192 @@
+"""GB300 space-time least-squares heat-equation solver (arXiv:1809.10026).
+
+Thin Python binding over the C ABI of include/stls.h: every step of the
+solver runs in libstls.so (CUDA, sm_103a).  PyTorch provides device memory
+and streams.  There is no CPU fallback: constructing a Solver without the
+compiled library or without a CUDA device raises.
+"""
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import FACTOR, make_params
+
+__all__ = ["Solver", "SolveFn", "host_factor", "make_params"]
+
+
+def _check(rc, ctx=None):
+    if rc != _lib.STLS_OK:
+        lib = _lib.load()
+        msg = lib.stls_last_error(ctx).decode()
+        raise RuntimeError("stls error %d (%s): %s" % (rc, _lib.STATUS_NAMES.get(rc, "?"), msg))
+
+
+def host_factor(which, direction, d, p, n_el, **kw):
+    """A 1D factor computed by the library's host setup (no GPU needed)."""
+    prm = make_params(d, p, n_el, **kw)
+    lib = _lib.load()
+    n_s = [n + prm.p_s - 2 for n in list(prm.n_el_s)[:d]]
+    n = n_s[direction] if direction < d else prm.n_el_t + prm.p_t - 1
+    size = n if FACTOR[which] in (4, 5, 6) else n * n
+    out = np.zeros(size)
+    rc = lib.stls_host_factor(ctypes.byref(prm), FACTOR[which], direction,
+                              out.ctypes.data_as(ctypes.c_void_p))
+    _check(rc)
+    return out if size == n else out.reshape(n, n)
+
+
+class Solver:
+    """Solver context for (0,1)^d x (0,T) with degree p splines and n_el elements.
+
+    precision: "fp64" or the mixed forms "tf32" / "bf16" (tensor-core FD
+    mode products, FP64 elsewhere).  Vectors are float64 CUDA tensors of
+    shape (batch, N) or (N,) for batch 1, in colexicographic order
+    (direction 1 fastest, time slowest).
+    """
+
+    def __init__(self, d, p, n_el, T=1.0, precision="fp64", flexible=None, batch=1, p_t=None,
+                 n_el_t=None, time_pencil="physical", device=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("stls.Solver needs a CUDA device (no CPU fallback)")
+        self.torch = torch
+        self.device = torch.device("cuda" if device is None else device)
+        self.lib = _lib.load()
+        self.params = make_params(d, p, n_el, T, precision, flexible, batch, p_t, n_el_t, time_pencil)
+        self.ctx = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            stream = torch.cuda.current_stream(self.device).cuda_stream
+            rc = self.lib.stls_create(ctypes.byref(self.ctx), ctypes.byref(self.params),
+                                      ctypes.c_void_p(stream))
+        if rc != _lib.STLS_OK:
+            raise RuntimeError("stls_create failed (%d): %s" % (rc, self.lib.stls_last_error(None).decode()))
+        n_s = (ctypes.c_int * 3)()
+        n_t, n_dof, b = ctypes.c_int(), ctypes.c_longlong(), ctypes.c_int()
+        self.lib.stls_sizes(self.ctx, n_s, ctypes.byref(n_t), ctypes.byref(n_dof), ctypes.byref(b))
+        self.d = d
+        self.n_s = [n_s[k] for k in range(d)]
+        self.n_t = n_t.value
+        self.N = n_dof.value
+        self.N_s = self.N // self.n_t
+        self.batch = b.value
+        self.precision = precision
+
+    # ---- marshalling ------------------------------------------------------------------
+    def _stream(self):
+        s = self.torch.cuda.current_stream(self.device).cuda_stream
+        self.lib.stls_set_stream(self.ctx, ctypes.c_void_p(s))
+
+    def _vec(self, x, n, name):
+        t = self.torch
+        if not isinstance(x, t.Tensor) or x.dtype != t.float64 or x.device.type != "cuda":
+            raise TypeError("%s must be a float64 CUDA tensor" % name)
+        if x.numel() != self.batch * n:
+            raise ValueError("%s must have batch * %d = %d entries, got %d" % (name, n, self.batch * n, x.numel()))
+        return x.contiguous()
+
+    def _out(self, like_shape, n):
+        return self.torch.empty((self.batch, n) if self.batch > 1 else (n,), dtype=self.torch.float64,
+                                device=self.device)
+
+    @staticmethod
+    def _ptr(x):
+        return ctypes.c_void_p(x.data_ptr())
+
+    # ---- operators -------------------------------------------------------------------
+    def apply_A(self, x, out=None):
+        x = self._vec(x, self.N, "x")
+        y = self._out(x.shape, self.N) if out is None else out
+        self._stream()
+        _check(self.lib.stls_apply_A(self.ctx, self._ptr(x), self._ptr(y)), self.ctx)
+        return y
+
+    def apply_precond(self, r, out=None):
+        r = self._vec(r, self.N, "r")
+        z = self._out(r.shape, self.N) if out is None else out
+        self._stream()
+        _check(self.lib.stls_apply_precond(self.ctx, self._ptr(r), self._ptr(z)), self.ctx)
+        return z
+
+    def solve(self, F, tol=1e-8, maxit=500, out=None, check=True):
+        F = self._vec(F, self.N, "F")
+        u = self._out(F.shape, self.N) if out is None else out
+        info = (_lib.SolveInfo * self.batch)()
+        self._stream()
+        rc = self.lib.stls_solve(self.ctx, self._ptr(F), self._ptr(u), float(tol), int(maxit), info)
+        infos = [info[b].as_dict() for b in range(self.batch)]
+        if check and rc not in (_lib.STLS_OK,):
+            _check(rc, self.ctx)
+        return u, infos
+
+    def solve_host(self, F, tol=1e-8, maxit=500, u=None):
+        """F, u: float64 numpy arrays (pinned memory is faster) of batch * N entries."""
+        F = np.ascontiguousarray(F, dtype=np.float64)
+        if F.size != self.batch * self.N:
+            raise ValueError("F has the wrong size")
+        u = np.empty_like(F) if u is None else u
+        info = (_lib.SolveInfo * self.batch)()
+        self._stream()
+        rc = self.lib.stls_solve_host(self.ctx, F.ctypes.data_as(ctypes.c_void_p),
+                                      u.ctypes.data_as(ctypes.c_void_p), float(tol), int(maxit), info)
+        _check(rc, self.ctx)
+        return u, [info[b].as_dict() for b in range(self.batch)]
+
+    def solve_host_ptr(self, F_ptr, u_ptr, tol=1e-8, maxit=500):
+        """Same as solve_host with raw host pointers (e.g. pinned torch tensors)."""
+        info = (_lib.SolveInfo * self.batch)()
+        self._stream()
+        rc = self.lib.stls_solve_host(self.ctx, ctypes.c_void_p(F_ptr), ctypes.c_void_p(u_ptr),
+                                      float(tol), int(maxit), info)
+        _check(rc, self.ctx)
+        return [info[b].as_dict() for b in range(self.batch)]
+
+    def apply_lift(self, c0):
+        c0 = self._vec(c0, self.N_s, "c0")
+        y = self._out(c0.shape, self.N)
+        self._stream()
+        _check(self.lib.stls_apply_lift(self.ctx, self._ptr(c0), self._ptr(y)), self.ctx)
+        return y
+
+    def lift_adjoint(self, g, lam):
+        g = self._vec(g, self.N, "g")
+        lam = self._vec(lam, self.N, "lam")
+        dc0 = self._out(g.shape, self.N_s)
+        self._stream()
+        _check(self.lib.stls_lift_adjoint(self.ctx, self._ptr(g), self._ptr(lam), self._ptr(dc0)), self.ctx)
+        return dc0
+
+    def factor(self, which, direction):
+        n = self.n_s[direction] if direction < self.d else self.n_t
+        size = n if FACTOR[which] in (4, 5, 6) else n * n
+        out = np.zeros(size)
+        _check(self.lib.stls_get_factor(self.ctx, FACTOR[which], direction,
+                                        out.ctypes.data_as(ctypes.c_void_p)), self.ctx)
+        return out if size == n else out.reshape(n, n)
+
+    def launch_count(self):
+        return int(self.lib.stls_launch_count(self.ctx))
+
+    def enable_timing(self, on=True):
+        _check(self.lib.stls_enable_timing(self.ctx, int(on)), self.ctx)
+
+    def phase_times(self):
+        ms = (ctypes.c_double * 3)()
+        cnt = (ctypes.c_longlong * 3)()
+        _check(self.lib.stls_phase_times(self.ctx, ms, cnt), self.ctx)
+        names = ["apply_A", "precond", "cg_vectors"]
+        return {names[i]: (ms[i], cnt[i]) for i in range(3)}
+
+    def close(self):
+        if getattr(self, "ctx", None) and self.ctx.value:
+            self.lib.stls_destroy(self.ctx)
+            self.ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+from .autograd import SolveFn  # noqa: E402

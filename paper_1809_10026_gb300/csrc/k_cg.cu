@@ -1,0 +1,343 @@
+// FP64 vector kernels of the (flexible) preconditioned CG method and their
+// inner products (Sec. 4.2: CG on the SPD system; Sec. 5: tolerance on the
+// relative residual, zero initial guess).
+//
+// Reductions are deterministic: every block of the (grid x batch) launch
+// writes its partial sums, and the last block to finish (atomic ticket) adds
+// the partials in index order and updates the per-right-hand-side CG scalars
+// on the device.  No kernel waits on another block.
+#include <cmath>
+
+#include "kernels.h"
+
+namespace stls {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sums of NV values, result valid in thread 0.
+template <int NV>
+__device__ void block_sum(double (&v)[NV]) {
+  __shared__ double sh[NV][kThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double s = warp_sum(v[k]);
+    if (lane == 0) sh[k][wid] = s;
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double s = lane < kThreads / 32 ? sh[k][lane] : 0.0;
+      v[k] = warp_sum(s);
+    }
+  }
+  __syncthreads();
+}
+
+// Writes this block's partial sums; returns true in every thread of the last
+// block of this right-hand side, with `tot` holding the ordered total.
+template <int NV>
+__device__ bool grid_sum(double (&v)[NV], RedWork rw, int b, double (&tot)[NV]) {
+  __shared__ bool is_last;
+  block_sum<NV>(v);
+  if (threadIdx.x == 0) {
+    double *dst = rw.partials + (static_cast<size_t>(b) * rw.grid + blockIdx.x) * 2;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) dst[k] = v[k];
+    __threadfence();
+    unsigned t = atomicAdd(rw.tickets + b, 1u);
+    is_last = (t == static_cast<unsigned>(rw.grid - 1));
+  }
+  __syncthreads();
+  if (!is_last) return false;
+  __threadfence();
+  double s[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) s[k] = 0.0;
+  const volatile double *src = rw.partials + static_cast<size_t>(b) * rw.grid * 2;
+  for (int g = threadIdx.x; g < rw.grid; g += kThreads)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) s[k] += src[g * 2 + k];
+  block_sum<NV>(s);
+  if (threadIdx.x == 0) rw.tickets[b] = 0u;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) tot[k] = s[k];
+  return true;
+}
+
+__global__ void __launch_bounds__(kThreads)
+    cg_init_kernel(const double *__restrict__ F, double *__restrict__ x, double *__restrict__ r,
+                   long long N, CGState *st, RedWork rw) {
+  const int b = blockIdx.y;
+  const double *Fb = F + static_cast<size_t>(b) * N;
+  double *xb = x + static_cast<size_t>(b) * N, *rb = r + static_cast<size_t>(b) * N;
+  double v[1] = {0.0};
+  for (long long i = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x; i < N;
+       i += static_cast<long long>(gridDim.x) * kThreads) {
+    double f = Fb[i];
+    xb[i] = 0.0;
+    rb[i] = f;
+    v[0] = fma(f, f, v[0]);
+  }
+  double tot[1];
+  if (grid_sum<1>(v, rw, b, tot) && threadIdx.x == 0) {
+    CGState &s = st[b];
+    s.nF2 = tot[0];
+    s.rr = tot[0];
+    s.iters = 0;
+    s.status = 0;
+    s.rel_res = 1.0;
+    s.true_rr = 0.0;
+    s.alpha = s.beta = s.pq = s.rz = 0.0;
+    s.active = 1;
+    if (!isfinite(tot[0])) {
+      s.status = STLS_ENONFINITE;
+      s.active = 0;
+    } else if (tot[0] == 0.0) {
+      s.rel_res = 0.0;
+      s.active = 0;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads)
+    cg_alpha_kernel(const double *__restrict__ p, const double *__restrict__ q, long long N,
+                    CGState *st, RedWork rw) {
+  const int b = blockIdx.y;
+  const double *pb = p + static_cast<size_t>(b) * N, *qb = q + static_cast<size_t>(b) * N;
+  double v[1] = {0.0};
+  for (long long i = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x; i < N;
+       i += static_cast<long long>(gridDim.x) * kThreads)
+    v[0] = fma(pb[i], qb[i], v[0]);
+  double tot[1];
+  if (grid_sum<1>(v, rw, b, tot) && threadIdx.x == 0) {
+    CGState &s = st[b];
+    if (!s.active) return;
+    s.pq = tot[0];
+    if (!isfinite(tot[0])) {
+      s.status = STLS_ENONFINITE;
+      s.active = 0;
+    } else if (!(tot[0] > 0.0)) {
+      s.status = STLS_EBREAKDOWN;
+      s.active = 0;
+    } else {
+      s.alpha = s.rz / tot[0];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads)
+    cg_xr_kernel(double *__restrict__ x, double *__restrict__ r, const double *__restrict__ p,
+                 const double *__restrict__ q, long long N, double tol, CGState *st, RedWork rw) {
+  const int b = blockIdx.y;
+  const bool active = st[b].active != 0;
+  const double alpha = st[b].alpha;
+  double *xb = x + static_cast<size_t>(b) * N, *rb = r + static_cast<size_t>(b) * N;
+  const double *pb = p + static_cast<size_t>(b) * N, *qb = q + static_cast<size_t>(b) * N;
+  double v[1] = {0.0};
+  if (active) {
+    for (long long i = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x; i < N;
+         i += static_cast<long long>(gridDim.x) * kThreads) {
+      xb[i] = fma(alpha, pb[i], xb[i]);
+      double ri = fma(-alpha, qb[i], rb[i]);
+      rb[i] = ri;
+      v[0] = fma(ri, ri, v[0]);
+    }
+  }
+  double tot[1];
+  if (grid_sum<1>(v, rw, b, tot) && threadIdx.x == 0) {
+    CGState &s = st[b];
+    if (!s.active) return;
+    s.iters += 1;
+    s.rr = tot[0];
+    s.rel_res = sqrt(tot[0] / s.nF2);
+    if (!isfinite(tot[0])) {
+      s.status = STLS_ENONFINITE;
+      s.active = 0;
+    } else if (s.rel_res <= tol) {
+      s.active = 0;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads)
+    cg_beta_kernel(const double *__restrict__ z, const double *__restrict__ r,
+                   const double *__restrict__ q, long long N, int flexible, int first, CGState *st,
+                   RedWork rw) {
+  const int b = blockIdx.y;
+  const double *zb = z + static_cast<size_t>(b) * N, *rb = r + static_cast<size_t>(b) * N;
+  const double *qb = q + static_cast<size_t>(b) * N;
+  const bool need_zq = flexible && !first;
+  double v[2] = {0.0, 0.0};
+  for (long long i = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x; i < N;
+       i += static_cast<long long>(gridDim.x) * kThreads) {
+    double zi = zb[i];
+    v[0] = fma(zi, rb[i], v[0]);
+    if (need_zq) v[1] = fma(zi, qb[i], v[1]);
+  }
+  double tot[2];
+  if (grid_sum<2>(v, rw, b, tot) && threadIdx.x == 0) {
+    CGState &s = st[b];
+    if (!s.active) return;
+    const double zr = tot[0];
+    if (!isfinite(zr) || !isfinite(tot[1])) {
+      s.status = STLS_ENONFINITE;
+      s.active = 0;
+      return;
+    }
+    if (!(zr > 0.0)) {
+      s.status = STLS_EBREAKDOWN;
+      s.active = 0;
+      return;
+    }
+    if (first) {
+      s.beta = 0.0;
+    } else if (flexible) {
+      // beta = (z_{k+1}, r_{k+1} - r_k) / (z_k, r_k) with r_{k+1} - r_k = -alpha q
+      s.beta = -s.alpha * tot[1] / s.rz;
+    } else {
+      s.beta = zr / s.rz;
+    }
+    s.rz = zr;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads)
+    cg_p_kernel(const double *__restrict__ z, double *__restrict__ p, long long N, int first,
+                const CGState *st) {
+  const int b = blockIdx.y;
+  if (!st[b].active) return;
+  const double beta = st[b].beta;
+  const double *zb = z + static_cast<size_t>(b) * N;
+  double *pb = p + static_cast<size_t>(b) * N;
+  for (long long i = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x; i < N;
+       i += static_cast<long long>(gridDim.x) * kThreads)
+    pb[i] = first ? zb[i] : fma(beta, pb[i], zb[i]);
+}
+
+__global__ void __launch_bounds__(kThreads)
+    true_residual_kernel(const double *__restrict__ F, const double *__restrict__ Ax, long long N,
+                         CGState *st, RedWork rw) {
+  const int b = blockIdx.y;
+  const double *Fb = F + static_cast<size_t>(b) * N, *Ab = Ax + static_cast<size_t>(b) * N;
+  double v[1] = {0.0};
+  for (long long i = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x; i < N;
+       i += static_cast<long long>(gridDim.x) * kThreads) {
+    double e = Fb[i] - Ab[i];
+    v[0] = fma(e, e, v[0]);
+  }
+  double tot[1];
+  if (grid_sum<1>(v, rw, b, tot) && threadIdx.x == 0) st[b].true_rr = tot[0];
+}
+
+__global__ void lift_combine_kernel(const double *__restrict__ Ls, const double *__restrict__ Js,
+                                    const double *__restrict__ e, const double *__restrict__ m,
+                                    double *__restrict__ y, long long Ns, int nt) {
+  const int b = blockIdx.y;
+  const long long N = Ns * nt;
+  for (long long i = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x; i < N;
+       i += static_cast<long long>(gridDim.x) * kThreads) {
+    long long t = i / Ns, c = i - t * Ns;
+    y[b * N + i] = e[t] * Ls[b * Ns + c] + m[t] * Js[b * Ns + c];
+  }
+}
+
+__global__ void lift_reduce_kernel(const double *__restrict__ lam, const double *__restrict__ g,
+                                   const double *__restrict__ e, const double *__restrict__ m,
+                                   double *__restrict__ a, double *__restrict__ bs,
+                                   double *__restrict__ gs, long long Ns, int nt) {
+  const int b = blockIdx.y;
+  const long long N = Ns * nt;
+  for (long long c = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x; c < Ns;
+       c += static_cast<long long>(gridDim.x) * kThreads) {
+    double sa = 0.0, sb = 0.0, sg = 0.0;
+    for (int t = 0; t < nt; ++t) {
+      double l = lam[b * N + t * Ns + c];
+      sa = fma(e[t], l, sa);
+      sb = fma(m[t], l, sb);
+      sg += g[b * N + t * Ns + c];
+    }
+    a[b * Ns + c] = sa;
+    bs[b * Ns + c] = sb;
+    gs[b * Ns + c] = sg;
+  }
+}
+
+__global__ void axpy_kernel(const double *__restrict__ x, const double *__restrict__ y, double alpha,
+                            double *__restrict__ out, long long n) {
+  for (long long i = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x; i < n;
+       i += static_cast<long long>(gridDim.x) * kThreads)
+    out[i] = fma(alpha, y[i], x[i]);
+}
+
+unsigned grid_1d(long long n) {
+  long long g = (n + kThreads - 1) / kThreads;
+  if (g > 152 * 16) g = 152 * 16;
+  return static_cast<unsigned>(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+int red_grid_for(long long n) {
+  long long g = (n + kThreads * 8 - 1) / (kThreads * 8);
+  if (g > 1024) g = 1024;
+  return static_cast<int>(g < 1 ? 1 : g);
+}
+
+cudaError_t launch_cg_init(const double *F, double *x, double *r, long long N, int B, CGState *st,
+                           RedWork rw, cudaStream_t s) {
+  cg_init_kernel<<<dim3(rw.grid, B), kThreads, 0, s>>>(F, x, r, N, st, rw);
+  return cudaGetLastError();
+}
+cudaError_t launch_cg_alpha(const double *p, const double *q, long long N, int B, CGState *st,
+                            RedWork rw, cudaStream_t s) {
+  cg_alpha_kernel<<<dim3(rw.grid, B), kThreads, 0, s>>>(p, q, N, st, rw);
+  return cudaGetLastError();
+}
+cudaError_t launch_cg_xr(double *x, double *r, const double *p, const double *q, long long N, int B,
+                         double tol, CGState *st, RedWork rw, cudaStream_t s) {
+  cg_xr_kernel<<<dim3(rw.grid, B), kThreads, 0, s>>>(x, r, p, q, N, tol, st, rw);
+  return cudaGetLastError();
+}
+cudaError_t launch_cg_beta(const double *z, const double *r, const double *q, long long N, int B,
+                           int flexible, int first, CGState *st, RedWork rw, cudaStream_t s) {
+  cg_beta_kernel<<<dim3(rw.grid, B), kThreads, 0, s>>>(z, r, q, N, flexible, first, st, rw);
+  return cudaGetLastError();
+}
+cudaError_t launch_cg_p(const double *z, double *p, long long N, int B, int first, CGState *st,
+                        cudaStream_t s) {
+  cg_p_kernel<<<dim3(grid_1d(N), B), kThreads, 0, s>>>(z, p, N, first, st);
+  return cudaGetLastError();
+}
+cudaError_t launch_true_residual(const double *F, const double *Ax, long long N, int B, CGState *st,
+                                 RedWork rw, cudaStream_t s) {
+  true_residual_kernel<<<dim3(rw.grid, B), kThreads, 0, s>>>(F, Ax, N, st, rw);
+  return cudaGetLastError();
+}
+cudaError_t launch_lift_combine(const double *Ls, const double *Js, const double *e, const double *m,
+                                double *y, long long Ns, int nt, int B, cudaStream_t s) {
+  lift_combine_kernel<<<dim3(grid_1d(Ns * nt), B), kThreads, 0, s>>>(Ls, Js, e, m, y, Ns, nt);
+  return cudaGetLastError();
+}
+cudaError_t launch_lift_reduce(const double *lam, const double *g, const double *e, const double *m,
+                               double *a, double *bsum, double *gsum, long long Ns, int nt, int B,
+                               cudaStream_t s) {
+  lift_reduce_kernel<<<dim3(grid_1d(Ns), B), kThreads, 0, s>>>(lam, g, e, m, a, bsum, gsum, Ns, nt);
+  return cudaGetLastError();
+}
+cudaError_t launch_axpy(const double *x, const double *y, double alpha, double *out, long long n,
+                        cudaStream_t s) {
+  axpy_kernel<<<grid_1d(n), kThreads, 0, s>>>(x, y, alpha, out, n);
+  return cudaGetLastError();
+}
+
+}  // namespace stls

@@ -1,0 +1,620 @@
+// C ABI of the solver (declared in include/stls.h): context creation, the
+// matrix-free system matrix (Eq. A_kron), the fast-diagonalization
+// preconditioner (Algorithm 1), the PCG / flexible-CG driver and the lifting
+// of a non-zero initial datum (Sec. 3.1).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "stls_internal.h"
+#include "tc_fd.h"
+
+namespace stls {
+int copy_factor_public(const HostSetup &hs, int which, int dir, double *out);
+}
+
+using stls::BandSpec;
+using stls::CGState;
+using stls::ModeView;
+
+struct stls_ctx {
+  stls::HostSetup hs;
+  cudaStream_t stream = nullptr;
+  int d = 0, B = 0, n_t = 0;
+  int n_s[3] = {1, 1, 1};
+  long long Ns = 0, N = 0;
+  // device factors
+  double *band_M[3] = {}, *band_K[3] = {}, *band_J[3] = {};
+  double *band_Kt = nullptr, *band_Mt = nullptr;
+  double *Uf[4] = {}, *Ub[4] = {};  // U^T (forward) and U (backward), row-major
+  double *lam_t = nullptr, *lam_s = nullptr;
+  double *e_end = nullptr, *m_int = nullptr;
+  // workspace
+  double *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr;
+  double *fd_tmp[2] = {};
+  double *abuf[8] = {};
+  double *ls_buf = nullptr;
+  double *lift_tmp[4] = {};
+  double *dF = nullptr, *du = nullptr;
+  CGState *st = nullptr, *st_host = nullptr;
+  stls::RedWork rw{};
+  stls::TcFd tc{};
+  std::vector<void *> allocations;
+  long long launches = 0;
+  std::string err;
+  // timing
+  bool timing = false;
+  double phase_ms[3] = {0, 0, 0};
+  long long phase_count[3] = {0, 0, 0};
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, int>> ev_pairs;  // (phase, first event index)
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+int set_err(stls_ctx *c, int code, const std::string &msg) {
+  if (c != nullptr) c->err = msg;
+  return code;
+}
+
+int cuda_err(stls_ctx *c, cudaError_t e, const char *where) {
+  return set_err(c, STLS_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define STLS_CK(call, where)                              \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return cuda_err(c, e_, where); \
+  } while (0)
+
+#define STLS_LAUNCH(call, where) \
+  do {                           \
+    c->launches += 1;            \
+    STLS_CK(call, where);        \
+  } while (0)
+
+template <typename T>
+int dev_alloc(stls_ctx *c, T **ptr, size_t count) {
+  void *v = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc(&v, count * sizeof(T));
+  if (e != cudaSuccess) return set_err(c, STLS_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  c->allocations.push_back(v);
+  *ptr = static_cast<T *>(v);
+  return STLS_OK;
+}
+
+template <typename T>
+int upload(stls_ctx *c, T **ptr, const std::vector<T> &h) {
+  int rc = dev_alloc(c, ptr, h.size());
+  if (rc) return rc;
+  STLS_CK(cudaMemcpy(*ptr, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice), "upload");
+  return STLS_OK;
+}
+
+std::vector<double> transpose(const std::vector<double> &A, int n) {
+  std::vector<double> T(A.size());
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) T[j * n + i] = A[i * n + j];
+  return T;
+}
+
+// ---- timing ---------------------------------------------------------------------------
+int phase_begin(stls_ctx *c, int phase) {
+  if (!c->timing) return -1;
+  size_t idx = c->ev_pairs.size() * 2;
+  while (c->ev_pool.size() < idx + 2) {
+    cudaEvent_t ev;
+    if (cudaEventCreate(&ev) != cudaSuccess) return -1;
+    c->ev_pool.push_back(ev);
+  }
+  cudaEventRecord(c->ev_pool[idx], c->stream);
+  c->ev_pairs.push_back({phase, static_cast<int>(idx)});
+  return static_cast<int>(idx);
+}
+
+void phase_end(stls_ctx *c, int idx) {
+  if (idx < 0) return;
+  cudaEventRecord(c->ev_pool[idx + 1], c->stream);
+}
+
+void collect_phases(stls_ctx *c) {
+  for (auto &pr : c->ev_pairs) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->ev_pool[pr.second], c->ev_pool[pr.second + 1]) == cudaSuccess) {
+      c->phase_ms[pr.first] += ms;
+      c->phase_count[pr.first] += 1;
+    }
+  }
+  c->ev_pairs.clear();
+}
+
+// ---- operators ------------------------------------------------------------------------
+ModeView spatial_view(const stls_ctx *c, int k, long long outer_mult) {
+  ModeView v{};
+  v.n = c->n_s[k];
+  long long inner = 1, outer = outer_mult;
+  for (int l = 0; l < k; ++l) inner *= c->n_s[l];
+  for (int l = k + 1; l < c->d; ++l) outer *= c->n_s[l];
+  v.inner = inner;
+  v.outer = outer;
+  v.in_outer_stride = v.out_outer_stride = static_cast<long long>(v.n) * inner;
+  return v;
+}
+
+// Spatial factors of Eq. A_kron on the cube, by the recurrence over modes
+// k = 1..d of the partial Kronecker products
+//   m  = M x ... x M,  j = sum (one J), k1 = sum (one K), kk = sum (two K's),
+// so that M_s = m, L_s = k1 and J_s = j + 2 kk after the last mode.  The
+// cross terms of J_s = int Lap B_i Lap B_j use int b''_i b_j = -K_ij on the
+// Dirichlet basis, so int d_kk B_i d_ll B_j = (K_k x K_l x M ...) for k != l.
+// X has `outer_mult` spatial slices.  Outputs (nullable): Ms, Js, Ls over all
+// slices, and Ls_last over the last time slice only (A x needs it for W_t).
+int spatial_tree(stls_ctx *c, const double *X, long long outer_mult, double *Ms, double *Js,
+                 double *Ls, double *Ls_last) {
+  const int d = c->d, p = c->hs.prm.p_s;
+  const double *cur[4] = {X, nullptr, nullptr, nullptr};  // m, j, k1, kk
+  for (int k = 0; k < d - 1; ++k) {
+    double **bank = c->abuf + (k % 2) * 4;
+    BandSpec s{};
+    s.p = p;
+    int slot_in[4] = {-1, -1, -1, -1};
+    for (int a = 0; a < 4; ++a)
+      if (cur[a] != nullptr) {
+        slot_in[a] = s.n_in;
+        s.in[s.n_in++] = cur[a];
+      }
+    const bool has_m = cur[0], has_j = cur[1], has_k1 = cur[2], has_kk = cur[3];
+    int slot_out[4] = {-1, -1, -1, -1};
+    const bool make[4] = {has_m, has_j || has_m, has_k1 || has_m, has_kk || has_k1};
+    for (int a = 0; a < 4; ++a)
+      if (make[a]) {
+        slot_out[a] = s.n_out;
+        s.out[s.n_out++] = bank[a];
+      }
+    auto add = [&](const double *band, int in_state, int out_state, double scale) {
+      if (slot_in[in_state] < 0 || slot_out[out_state] < 0) return;
+      s.term[s.n_terms++] = {band, slot_in[in_state], slot_out[out_state], scale};
+    };
+    add(c->band_M[k], 0, 0, 1.0);
+    add(c->band_M[k], 1, 1, 1.0);
+    add(c->band_J[k], 0, 1, 1.0);
+    add(c->band_M[k], 2, 2, 1.0);
+    add(c->band_K[k], 0, 2, 1.0);
+    add(c->band_M[k], 3, 3, 1.0);
+    add(c->band_K[k], 2, 3, 1.0);
+    STLS_LAUNCH(stls::launch_banded_f64(s, spatial_view(c, k, outer_mult), c->stream), "banded");
+    for (int a = 0; a < 4; ++a) cur[a] = make[a] ? bank[a] : nullptr;
+  }
+  const int k = d - 1;
+  {
+    BandSpec s{};
+    s.p = p;
+    int slot_in[4] = {-1, -1, -1, -1};
+    for (int a = 0; a < 4; ++a)
+      if (cur[a] != nullptr) {
+        slot_in[a] = s.n_in;
+        s.in[s.n_in++] = cur[a];
+      }
+    int o_ms = -1, o_js = -1, o_ls = -1;
+    if (Ms) { o_ms = s.n_out; s.out[s.n_out++] = Ms; }
+    if (Js) { o_js = s.n_out; s.out[s.n_out++] = Js; }
+    if (Ls) { o_ls = s.n_out; s.out[s.n_out++] = Ls; }
+    auto add = [&](const double *band, int in_state, int out_slot, double scale) {
+      if (slot_in[in_state] < 0 || out_slot < 0) return;
+      s.term[s.n_terms++] = {band, slot_in[in_state], out_slot, scale};
+    };
+    add(c->band_M[k], 0, o_ms, 1.0);
+    add(c->band_M[k], 1, o_js, 1.0);
+    add(c->band_M[k], 3, o_js, 2.0);
+    add(c->band_J[k], 0, o_js, 1.0);
+    add(c->band_K[k], 2, o_js, 2.0);
+    add(c->band_M[k], 2, o_ls, 1.0);
+    add(c->band_K[k], 0, o_ls, 1.0);
+    if (s.n_out > 0)
+      STLS_LAUNCH(stls::launch_banded_f64(s, spatial_view(c, k, outer_mult), c->stream), "banded");
+    if (Ls_last) {
+      // L_s on the last time slice of every right-hand side
+      BandSpec t{};
+      t.p = p;
+      const long long off = static_cast<long long>(c->n_t - 1) * c->Ns;
+      int sm_ = -1, sk1 = -1;
+      t.in[t.n_in] = cur[0] + off;
+      sm_ = t.n_in++;
+      if (cur[2]) {
+        t.in[t.n_in] = cur[2] + off;
+        sk1 = t.n_in++;
+      }
+      t.out[t.n_out++] = Ls_last;
+      t.term[t.n_terms++] = {c->band_K[k], sm_, 0, 1.0};
+      if (sk1 >= 0) t.term[t.n_terms++] = {c->band_M[k], sk1, 0, 1.0};
+      ModeView v = spatial_view(c, k, 1);
+      v.outer = c->B;
+      v.in_outer_stride = c->N;
+      v.out_outer_stride = c->Ns;
+      STLS_LAUNCH(stls::launch_banded_f64(t, v, c->stream), "banded");
+    }
+  }
+  return STLS_OK;
+}
+
+int apply_A_impl(stls_ctx *c, const double *x, double *y) {
+  const int bank = (c->d - 1) % 2;
+  double *Ms = c->abuf[bank * 4 + 0], *Js = c->abuf[bank * 4 + 1];
+  int rc = spatial_tree(c, x, static_cast<long long>(c->B) * c->n_t, Ms, Js, nullptr, c->ls_buf);
+  if (rc) return rc;
+  BandSpec s{};
+  s.p = c->hs.prm.p_t;
+  s.in[0] = Ms;
+  s.in[1] = Js;
+  s.n_in = 2;
+  s.out[0] = y;
+  s.n_out = 1;
+  s.term[0] = {c->band_Kt, 0, 0, 1.0};
+  s.term[1] = {c->band_Mt, 1, 0, 1.0};
+  s.n_terms = 2;
+  s.last_add = c->ls_buf;  // W_t x L_s: W_t = e_{n_t} e_{n_t}^T touches the last time slice only
+  s.last_out = 0;
+  ModeView v{};
+  v.n = c->n_t;
+  v.inner = c->Ns;
+  v.outer = c->B;
+  v.in_outer_stride = v.out_outer_stride = c->N;
+  STLS_LAUNCH(stls::launch_banded_f64(s, v, c->stream), "banded(time)");
+  return STLS_OK;
+}
+
+ModeView fd_view(const stls_ctx *c, int k) {
+  if (k < c->d) return spatial_view(c, k, static_cast<long long>(c->B) * c->n_t);
+  ModeView v{};
+  v.n = c->n_t;
+  v.inner = c->Ns;
+  v.outer = c->B;
+  v.in_outer_stride = v.out_outer_stride = c->N;
+  return v;
+}
+
+// Algorithm 1, steps 2-4: forward mode products with U_1^T..U_d^T, U_t^T, the
+// division by lambda_t[i_t] + sum_k lambda_k[i_k] (fused into the last forward
+// product), and backward mode products with U_1..U_d, U_t.
+int fd_apply_impl(stls_ctx *c, const double *r, double *z) {
+  if (c->hs.prm.precision != STLS_FP64) {
+    c->launches += stls::tc_fd_launch_count(c->tc);
+    cudaError_t e = stls::tc_fd_apply(c->tc, r, z, c->stream);
+    if (e != cudaSuccess) return cuda_err(c, e, "tensor-core FD apply");
+    return STLS_OK;
+  }
+  const int nprod = 2 * (c->d + 1);
+  const double *src = r;
+  for (int s = 0; s < nprod; ++s) {
+    const bool fwd = s <= c->d;
+    const int k = fwd ? s : s - c->d - 1;
+    double *dst = (s == nprod - 1) ? z : c->fd_tmp[s % 2];
+    const bool divide = fwd && k == c->d;
+    STLS_LAUNCH(stls::launch_modeprod_f64(src, dst, fwd ? c->Uf[k] : c->Ub[k], fd_view(c, k),
+                                          divide ? c->lam_t : nullptr, divide ? c->lam_s : nullptr,
+                                          c->stream),
+                "modeprod");
+    src = dst;
+  }
+  return STLS_OK;
+}
+
+int check_ptr(stls_ctx *c, const void *ptr, const char *name) {
+  if (ptr == nullptr || (reinterpret_cast<uintptr_t>(ptr) & 7u) != 0)
+    return set_err(c, STLS_EINVAL, std::string(name) + " is NULL or not 8-byte aligned");
+  return STLS_OK;
+}
+
+int solve_impl(stls_ctx *c, const double *F, double *u, double tol, int maxit, stls_solve_info *info) {
+  if (!(tol >= 0.0) || maxit < 0) return set_err(c, STLS_EINVAL, "tol must be >= 0 and maxit >= 0");
+  if (check_ptr(c, F, "F") || check_ptr(c, u, "u")) return STLS_EINVAL;
+  const long long N = c->N;
+  const int B = c->B;
+  const int flex = c->hs.prm.flexible;
+  int ph = phase_begin(c, 2);
+  STLS_LAUNCH(stls::launch_cg_init(F, u, c->r, N, B, c->st, c->rw, c->stream), "cg_init");
+  phase_end(c, ph);
+  ph = phase_begin(c, 1);
+  int rc = fd_apply_impl(c, c->r, c->z);
+  if (rc) return rc;
+  phase_end(c, ph);
+  ph = phase_begin(c, 2);
+  STLS_LAUNCH(stls::launch_cg_beta(c->z, c->r, c->q, N, B, flex, 1, c->st, c->rw, c->stream), "cg_beta");
+  STLS_LAUNCH(stls::launch_cg_p(c->z, c->p, N, B, 1, c->st, c->stream), "cg_p");
+  phase_end(c, ph);
+  for (int it = 1; it <= maxit; ++it) {
+    ph = phase_begin(c, 0);
+    rc = apply_A_impl(c, c->p, c->q);
+    if (rc) return rc;
+    phase_end(c, ph);
+    ph = phase_begin(c, 2);
+    STLS_LAUNCH(stls::launch_cg_alpha(c->p, c->q, N, B, c->st, c->rw, c->stream), "cg_alpha");
+    STLS_LAUNCH(stls::launch_cg_xr(u, c->r, c->p, c->q, N, B, tol, c->st, c->rw, c->stream), "cg_xr");
+    phase_end(c, ph);
+    STLS_CK(cudaMemcpyAsync(c->st_host, c->st, sizeof(CGState) * B, cudaMemcpyDeviceToHost, c->stream),
+            "state copy");
+    STLS_CK(cudaStreamSynchronize(c->stream), "sync");
+    bool any = false;
+    for (int b = 0; b < B; ++b) any = any || c->st_host[b].active;
+    if (!any) break;
+    ph = phase_begin(c, 1);
+    rc = fd_apply_impl(c, c->r, c->z);
+    if (rc) return rc;
+    phase_end(c, ph);
+    ph = phase_begin(c, 2);
+    STLS_LAUNCH(stls::launch_cg_beta(c->z, c->r, c->q, N, B, flex, 0, c->st, c->rw, c->stream), "cg_beta");
+    STLS_LAUNCH(stls::launch_cg_p(c->z, c->p, N, B, 0, c->st, c->stream), "cg_p");
+    phase_end(c, ph);
+  }
+  // true FP64 residual ||F - A u|| at exit
+  rc = apply_A_impl(c, u, c->q);
+  if (rc) return rc;
+  STLS_LAUNCH(stls::launch_true_residual(F, c->q, N, B, c->st, c->rw, c->stream), "true_residual");
+  STLS_CK(cudaMemcpyAsync(c->st_host, c->st, sizeof(CGState) * B, cudaMemcpyDeviceToHost, c->stream),
+          "state copy");
+  STLS_CK(cudaStreamSynchronize(c->stream), "sync");
+  if (c->timing) collect_phases(c);
+  int first_bad = STLS_OK;
+  for (int b = 0; b < B; ++b) {
+    const CGState &s = c->st_host[b];
+    int status = s.status;
+    if (status == STLS_OK && s.active) status = STLS_ENOTCONV;
+    if (info != nullptr) {
+      info[b].iters = s.iters;
+      info[b].status = status;
+      info[b].rel_res = s.rel_res;
+      info[b].true_rel_res = s.nF2 > 0 ? std::sqrt(s.true_rr / s.nF2) : 0.0;
+    }
+    if (status != STLS_OK && first_bad == STLS_OK) first_bad = status;
+  }
+  if (first_bad != STLS_OK) {
+    static const char *names[] = {"ok", "einval", "enomem", "ecuda", "not converged", "breakdown",
+                                  "non-finite value"};
+    set_err(c, first_bad, std::string("solve: ") + names[first_bad]);
+  }
+  return first_bad;
+}
+
+}  // namespace
+
+// ---- C ABI ----------------------------------------------------------------------------
+extern "C" {
+
+const char *stls_last_error(const stls_ctx *ctx) {
+  return ctx == nullptr ? g_create_error.c_str() : ctx->err.c_str();
+}
+
+void stls_destroy(stls_ctx *ctx) {
+  if (ctx == nullptr) return;
+  cudaStreamSynchronize(ctx->stream);
+  stls::tc_fd_destroy(ctx->tc);
+  for (void *v : ctx->allocations) cudaFree(v);
+  if (ctx->st_host) cudaFreeHost(ctx->st_host);
+  for (cudaEvent_t ev : ctx->ev_pool) cudaEventDestroy(ev);
+  delete ctx;
+}
+
+int stls_create(stls_ctx **out, const stls_params *prm, void *cuda_stream) {
+  g_create_error.clear();
+  if (out == nullptr || prm == nullptr) {
+    g_create_error = "out and prm must not be NULL";
+    return STLS_EINVAL;
+  }
+  *out = nullptr;
+  stls_ctx *c = new stls_ctx();
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  std::string err;
+  if (!stls::build_setup(*prm, c->hs, err)) {
+    g_create_error = err;
+    delete c;
+    return STLS_EINVAL;
+  }
+  const stls_params &P = c->hs.prm;
+  c->d = P.d;
+  c->B = P.batch;
+  c->n_t = c->hs.time.n;
+  c->Ns = 1;
+  for (int k = 0; k < c->d; ++k) {
+    c->n_s[k] = c->hs.space[k].n;
+    c->Ns *= c->n_s[k];
+  }
+  c->N = c->Ns * c->n_t;
+  auto fail = [&](int code) {
+    g_create_error = c->err;
+    stls_destroy(c);
+    return code;
+  };
+  int rc = STLS_OK;
+  for (int k = 0; k < c->d && !rc; ++k) {
+    const stls::Dir1D &D = c->hs.space[k];
+    rc = upload(c, &c->band_M[k], stls::to_band(D.M, D.n, D.p));
+    if (!rc) rc = upload(c, &c->band_K[k], stls::to_band(D.K, D.n, D.p));
+    if (!rc) rc = upload(c, &c->band_J[k], stls::to_band(D.J, D.n, D.p));
+    if (!rc) rc = upload(c, &c->Uf[k], transpose(c->hs.eig_s[k].U, D.n));
+    if (!rc) rc = upload(c, &c->Ub[k], c->hs.eig_s[k].U);
+  }
+  const stls::Dir1D &Tm = c->hs.time;
+  if (!rc) rc = upload(c, &c->band_Kt, stls::to_band(Tm.K, Tm.n, Tm.p));
+  if (!rc) rc = upload(c, &c->band_Mt, stls::to_band(Tm.M, Tm.n, Tm.p));
+  if (!rc) rc = upload(c, &c->Uf[c->d], transpose(c->hs.eig_t.U, Tm.n));
+  if (!rc) rc = upload(c, &c->Ub[c->d], c->hs.eig_t.U);
+  if (!rc) rc = upload(c, &c->lam_t, c->hs.eig_t.lam);
+  if (!rc) rc = upload(c, &c->e_end, Tm.end_values);
+  if (!rc) rc = upload(c, &c->m_int, Tm.integrals);
+  if (!rc) {
+    // lambda_s[c] = sum_k lambda_k[i_k(c)] over the colexicographic spatial index
+    std::vector<double> ls(c->Ns, 0.0);
+    for (long long idx = 0; idx < c->Ns; ++idx) {
+      long long rem = idx;
+      double s = 0.0;
+      for (int k = 0; k < c->d; ++k) {
+        s += c->hs.eig_s[k].lam[rem % c->n_s[k]];
+        rem /= c->n_s[k];
+      }
+      ls[idx] = s;
+    }
+    rc = upload(c, &c->lam_s, ls);
+  }
+  if (rc) return fail(rc);
+  const size_t BN = static_cast<size_t>(c->B) * c->N, BNs = static_cast<size_t>(c->B) * c->Ns;
+  double **vecs[] = {&c->r, &c->p, &c->q, &c->z, &c->fd_tmp[0], &c->fd_tmp[1], &c->dF, &c->du};
+  for (double **v : vecs)
+    if (!rc) rc = dev_alloc(c, v, BN);
+  for (int a = 0; a < 8 && !rc; ++a) rc = dev_alloc(c, &c->abuf[a], BN);
+  if (!rc) rc = dev_alloc(c, &c->ls_buf, BNs);
+  for (int a = 0; a < 4 && !rc; ++a) rc = dev_alloc(c, &c->lift_tmp[a], BNs);
+  if (!rc) rc = dev_alloc(c, &c->st, c->B);
+  c->rw.grid = stls::red_grid_for(c->N);
+  if (!rc) rc = dev_alloc(c, &c->rw.partials, static_cast<size_t>(c->B) * c->rw.grid * 2);
+  if (!rc) rc = dev_alloc(c, &c->rw.tickets, c->B);
+  if (rc) return fail(rc);
+  if (cudaMallocHost(&c->st_host, sizeof(CGState) * c->B) != cudaSuccess) {
+    c->st_host = nullptr;
+    c->err = "cudaMallocHost failed";
+    return fail(STLS_ENOMEM);
+  }
+  if (cudaMemset(c->rw.tickets, 0, sizeof(unsigned) * c->B) != cudaSuccess ||
+      cudaMemset(c->st, 0, sizeof(CGState) * c->B) != cudaSuccess) {
+    c->err = "cudaMemset failed";
+    return fail(STLS_ECUDA);
+  }
+  if (P.precision != STLS_FP64) {
+    std::vector<std::vector<double>> U(c->d + 1);
+    std::vector<int> n(c->d + 1);
+    for (int k = 0; k < c->d; ++k) {
+      U[k] = c->hs.eig_s[k].U;
+      n[k] = c->n_s[k];
+    }
+    U[c->d] = c->hs.eig_t.U;
+    n[c->d] = c->n_t;
+    std::string tcerr;
+    cudaError_t e = stls::tc_fd_create(c->tc, P.precision, c->d, n.data(), c->B, U, c->lam_t, c->lam_s,
+                                       tcerr);
+    if (e != cudaSuccess || !tcerr.empty()) {
+      c->err = tcerr.empty() ? std::string("tensor-core FD setup: ") + cudaGetErrorString(e) : tcerr;
+      return fail(tcerr.empty() ? STLS_ECUDA : STLS_EINVAL);
+    }
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    c->err = "device synchronize after setup failed";
+    return fail(STLS_ECUDA);
+  }
+  *out = c;
+  return STLS_OK;
+}
+
+int stls_set_stream(stls_ctx *c, void *cuda_stream) {
+  if (c == nullptr) return STLS_EINVAL;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  return STLS_OK;
+}
+
+int stls_sizes(const stls_ctx *c, int *n_s, int *n_t, long long *n_dof, int *batch) {
+  if (c == nullptr) return STLS_EINVAL;
+  if (n_s)
+    for (int k = 0; k < c->d; ++k) n_s[k] = c->n_s[k];
+  if (n_t) *n_t = c->n_t;
+  if (n_dof) *n_dof = c->N;
+  if (batch) *batch = c->B;
+  return STLS_OK;
+}
+
+int stls_apply_A(stls_ctx *c, const double *x, double *y) {
+  if (c == nullptr) return STLS_EINVAL;
+  if (check_ptr(c, x, "x") || check_ptr(c, y, "y")) return STLS_EINVAL;
+  if (x == y) return set_err(c, STLS_EINVAL, "apply_A: x and y must not overlap");
+  return apply_A_impl(c, x, y);
+}
+
+int stls_apply_precond(stls_ctx *c, const double *r, double *z) {
+  if (c == nullptr) return STLS_EINVAL;
+  if (check_ptr(c, r, "r") || check_ptr(c, z, "z")) return STLS_EINVAL;
+  return fd_apply_impl(c, r, z);
+}
+
+int stls_solve(stls_ctx *c, const double *F, double *u, double tol, int maxit, stls_solve_info *info) {
+  if (c == nullptr) return STLS_EINVAL;
+  if (F == u) return set_err(c, STLS_EINVAL, "solve: F and u must not overlap");
+  return solve_impl(c, F, u, tol, maxit, info);
+}
+
+int stls_solve_host(stls_ctx *c, const double *F_host, double *u_host, double tol, int maxit,
+                    stls_solve_info *info) {
+  if (c == nullptr || F_host == nullptr || u_host == nullptr) return set_err(c, STLS_EINVAL, "NULL argument");
+  const size_t bytes = sizeof(double) * static_cast<size_t>(c->B) * c->N;
+  STLS_CK(cudaMemcpyAsync(c->dF, F_host, bytes, cudaMemcpyHostToDevice, c->stream), "H2D copy of F");
+  int rc = solve_impl(c, c->dF, c->du, tol, maxit, info);
+  if (rc != STLS_OK && rc != STLS_ENOTCONV && rc != STLS_EBREAKDOWN && rc != STLS_ENONFINITE) return rc;
+  STLS_CK(cudaMemcpyAsync(u_host, c->du, bytes, cudaMemcpyDeviceToHost, c->stream), "D2H copy of u");
+  STLS_CK(cudaStreamSynchronize(c->stream), "sync");
+  return rc;
+}
+
+int stls_apply_lift(stls_ctx *c, const double *c0, double *y) {
+  if (c == nullptr) return STLS_EINVAL;
+  if (check_ptr(c, c0, "c0") || check_ptr(c, y, "y")) return STLS_EINVAL;
+  double *Js = c->lift_tmp[0], *Ls = c->lift_tmp[1];
+  int rc = spatial_tree(c, c0, c->B, nullptr, Js, Ls, nullptr);
+  if (rc) return rc;
+  STLS_LAUNCH(stls::launch_lift_combine(Ls, Js, c->e_end, c->m_int, y, c->Ns, c->n_t, c->B, c->stream),
+              "lift_combine");
+  return STLS_OK;
+}
+
+int stls_lift_adjoint(stls_ctx *c, const double *g, const double *lam, double *dc0) {
+  if (c == nullptr) return STLS_EINVAL;
+  if (check_ptr(c, g, "g") || check_ptr(c, lam, "lam") || check_ptr(c, dc0, "dc0")) return STLS_EINVAL;
+  // G^T lam = L_s (sum_t e_t lam_t) + J_s (sum_t m_t lam_t)   (L_s, J_s symmetric)
+  double *a = c->lift_tmp[0], *bs = c->lift_tmp[1], *gs = c->lift_tmp[2];
+  STLS_LAUNCH(stls::launch_lift_reduce(lam, g, c->e_end, c->m_int, a, bs, gs, c->Ns, c->n_t, c->B,
+                                       c->stream),
+              "lift_reduce");
+  double *La = c->ls_buf;           // B x N_s
+  double *Jb = c->lift_tmp[3];
+  int rc = spatial_tree(c, a, c->B, nullptr, nullptr, La, nullptr);
+  if (rc) return rc;
+  rc = spatial_tree(c, bs, c->B, nullptr, Jb, nullptr, nullptr);
+  if (rc) return rc;
+  const long long n = static_cast<long long>(c->B) * c->Ns;
+  STLS_LAUNCH(stls::launch_axpy(gs, La, -1.0, dc0, n, c->stream), "axpy");
+  STLS_LAUNCH(stls::launch_axpy(dc0, Jb, -1.0, dc0, n, c->stream), "axpy");
+  return STLS_OK;
+}
+
+int stls_get_factor(const stls_ctx *c, int which, int dir, double *host_out) {
+  if (c == nullptr) return STLS_EINVAL;
+  return stls::copy_factor_public(c->hs, which, dir, host_out);
+}
+
+long long stls_launch_count(const stls_ctx *c) { return c == nullptr ? 0 : c->launches; }
+
+int stls_enable_timing(stls_ctx *c, int on) {
+  if (c == nullptr) return STLS_EINVAL;
+  c->timing = on != 0;
+  for (int i = 0; i < 3; ++i) {
+    c->phase_ms[i] = 0.0;
+    c->phase_count[i] = 0;
+  }
+  c->ev_pairs.clear();
+  return STLS_OK;
+}
+
+int stls_phase_times(stls_ctx *c, double *ms_out3, long long *count_out3) {
+  if (c == nullptr) return STLS_EINVAL;
+  for (int i = 0; i < 3; ++i) {
+    if (ms_out3) ms_out3[i] = c->phase_ms[i];
+    if (count_out3) count_out3[i] = c->phase_count[i];
+  }
+  return STLS_OK;
+}
+
+}  // extern "C"

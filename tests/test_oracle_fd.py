@@ -94,3 +94,19 @@ def test_pcg_matches_direct_solve(flexible):
     x, it, _ = pcg(lambda v: A @ v, FD(prob).apply, F, 1e-13, 200, flexible)
     np.testing.assert_allclose(x, x_ref, rtol=0, atol=1e-10 * np.abs(x_ref).max())
     np.testing.assert_allclose(prob.apply_A_kron(x), A @ x, rtol=1e-13, atol=1e-12)
+
+
+@pytest.mark.parametrize("n_el,p", [(32, 4), (64, 3)])
+def test_smallest_eigenvalues_to_high_relative_accuracy(n_el, p):
+    """The eigenvalues that P^{-1} amplifies most, against 40-digit arithmetic."""
+    mp = pytest.importorskip("mpmath")
+    from oracle.fd import generalized_eig
+    from oracle.spaces import Direction1D
+    mp.mp.dps = 40
+    s = Direction1D(n_el, p, "space")
+    L = mp.cholesky(mp.matrix(s.M.tolist()))
+    Li = L ** -1
+    ref = sorted(float(e) for e in mp.eigsy(Li * mp.matrix(s.J.tolist()) * Li.T, eigvals_only=True))
+    lam, _ = generalized_eig(s.J, s.M)
+    np.testing.assert_allclose(lam[:5], ref[:5], rtol=1e-11)
+    np.testing.assert_allclose(lam, ref, rtol=1e-10)
