@@ -218,3 +218,44 @@ class STProblem:
                 Z = self.mode_product(Z, sd[m].K if m == k else sd[m].M, m + 1)
             Y += self.mode_product(Z, tm.W, d + 1)
         return Y.reshape(-1)
+
+
+def apply_A_rows(prob, x, rows):
+    """(A x)[rows] for sampled row indices, term by term from Eq. A_kron.
+
+    Each row of a Kronecker term is the product of 1D rows, so an entry needs
+    only the (2p+1)^(d+1) neighbours of the row's multi-index.  Used to check
+    A x at sizes where the full product is too slow in plain numpy.
+    """
+    d, tm, sd = prob.d, prob.time, prob.space
+    X = x.reshape(prob.shape)
+    out = np.zeros(len(rows))
+    terms = [([s.M for s in sd], tm.K), ]
+    for k in range(d):
+        for l in range(d):
+            mats = [s.M for s in sd]
+            if k == l:
+                mats[k] = sd[k].J
+            else:
+                mats[k] = sd[k].D2
+                mats[l] = sd[l].D2.T
+            terms.append((mats, tm.M))
+    for k in range(d):
+        mats = [s.M for s in sd]
+        mats[k] = sd[k].K
+        terms.append((mats, tm.W))
+    p_axes = [prob.p_t] + [prob.p_s] * d            # band half-widths per C-order axis
+    for r, row in enumerate(rows):
+        idx = np.unravel_index(row, prob.shape)   # (i_t, i_d, ..., i_1)
+        win = [slice(max(0, i - pa), min(n, i + pa + 1)) for i, pa, n in zip(idx, p_axes, prob.shape)]
+        Xw = X[tuple(win)]
+        it, isp = idx[0], idx[1:][::-1]           # isp = (i_1, ..., i_d)
+        wsp = win[1:][::-1]
+        total = 0.0
+        for mats, Tt in terms:
+            Y = np.tensordot(Tt[it, win[0]], Xw, axes=([0], [0]))
+            for k in range(d - 1, -1, -1):
+                Y = np.tensordot(mats[k][isp[k], wsp[k]], Y, axes=([0], [0]))
+            total += float(Y)
+        out[r] = total
+    return out

@@ -109,3 +109,13 @@ def test_convergence_rates(p, norm, rate):
         errs.append(errors(prob, u, exact)[norm])
     observed = np.log2(errs[-2] / errs[-1])
     assert abs(observed - rate) < 0.35, (errs, observed)
+
+
+@pytest.mark.parametrize("d,p,n_el", [(1, 2, 5), (2, 3, 4), (3, 2, 3)])
+def test_sampled_rows_of_A(d, p, n_el):
+    from oracle.system import apply_A_rows
+    prob = STProblem(d, p, n_el, 0.8)
+    x = np.random.default_rng(0).standard_normal(prob.N)
+    y = prob.assemble_A_kron() @ x
+    np.testing.assert_allclose(apply_A_rows(prob, x, np.arange(prob.N)), y, atol=1e-13 * np.abs(y).max())
+    np.testing.assert_allclose(prob.apply_A_kron(x), y, atol=1e-13 * np.abs(y).max())
