@@ -343,6 +343,8 @@ int solve_impl(stls_ctx *c, const double *F, double *u, double tol, int maxit, s
     STLS_CK(cudaMemcpyAsync(c->st_host, c->st, sizeof(CGState) * B, cudaMemcpyDeviceToHost, c->stream),
             "state copy");
     STLS_CK(cudaStreamSynchronize(c->stream), "sync");
+    if (c->hs.prm.precision != STLS_FP64 && stls::tc_fd_error(c->tc))
+      return set_err(c, STLS_ECUDA, "tensor-core FD apply: a bounded mbarrier wait timed out");
     bool any = false;
     for (int b = 0; b < B; ++b) any = any || c->st_host[b].active;
     if (!any) break;

@@ -28,6 +28,9 @@ cudaError_t tc_fd_create(TcFd &tc, int precision, int d, const int *n, int B,
                          const double *lam_s_dev, std::string &err);
 cudaError_t tc_fd_apply(TcFd &tc, const double *r, double *z, cudaStream_t s);
 int tc_fd_launch_count(const TcFd &tc);
+// Non-zero once a tensor-core kernel gave up on a bounded wait (host-mapped
+// flag; read it after synchronizing the stream).
+int tc_fd_error(const TcFd &tc);
 void tc_fd_destroy(TcFd &tc);
 
 }  // namespace stls

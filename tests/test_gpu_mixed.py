@@ -1,0 +1,92 @@
+"""GPU parity of the mixed-precision (tensor-core) preconditioner and solves.
+
+The tensor-core FD apply is compared with oracle.mixed, which applies the
+same BF16/TF32 operand roundings, FP32 accumulation and intermediate storage
+formats.  The two differ in how the FP32 sums are rounded: the tensor core's
+accumulator is not a correctly rounded FP32 sum of the K products, and the
+products with the M-orthonormal eigenvector matrices cancel strongly (entries
+of U grow like h^{-1/2}), so a few FP32 ulps per product become ~5e-5
+normwise after 2(d+1) products.  A differently rounded BF16 intermediate
+flips by one BF16 ulp now and then.  Normwise bounds: BF16 <= 2e-3, TF32 <=
+2e-4 against the model, and against exact FP64 Algorithm 1 (the model's own
+error is ~1e-2 / ~1e-3): BF16 <= 3e-2, TF32 <= 3e-3.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle.system import STProblem
+from oracle.fd import FD
+from oracle import mixed
+from paper_1809_10026_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL_MODEL = {"bf16": 2e-3, "tf32": 2e-4}
+TOL_EXACT = {"bf16": 3e-2, "tf32": 3e-3}
+
+
+def _solver(*a, **k):
+    import paper_1809_10026_gb300 as stls
+    return stls.Solver(*a, **k)
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("form", ["bf16", "tf32"])
+@pytest.mark.parametrize("d,p,n_el,batch", [(1, 2, 7, 1), (2, 3, 6, 3), (2, 5, 9, 1), (3, 2, 4, 2),
+                                            (3, 3, 9, 1), (3, 4, 12, 1)])
+def test_tc_precond_matches_model(form, d, p, n_el, batch):
+    prob = STProblem(d, p, n_el)
+    fd = FD(prob)
+    S = _solver(d, p, n_el, precision=form, batch=batch)
+    r = synth.uniform(prob.N, 500 + d + p, batch=batch).reshape(batch, prob.N)
+    z = S.apply_precond(torch.from_numpy(r).cuda()).cpu().numpy().reshape(batch, prob.N)
+    for b in range(batch):
+        model = mixed.apply_mixed(fd, r[b], form)
+        exact = fd.apply(r[b])
+        assert _rel(z[b], model) <= TOL_MODEL[form], (_rel(z[b], model), _rel(z[b], exact))
+        assert _rel(z[b], exact) <= TOL_EXACT[form]
+
+
+@pytest.mark.parametrize("form", ["bf16", "tf32"])
+def test_tc_precond_full_size_cfg4(form):
+    prob = STProblem(3, 3, 64)
+    fd = FD(prob)
+    S = _solver(3, 3, 64, precision=form)
+    r = synth.uniform(prob.N, 4)
+    z = S.apply_precond(torch.from_numpy(r).cuda()).cpu().numpy()
+    assert _rel(z, fd.apply(r)) <= TOL_EXACT[form]
+
+
+@pytest.mark.parametrize("form", ["bf16", "tf32"])
+def test_mixed_solve_cfg3(form):
+    """3D, p = 4, 32 elements (1,375,640 DoF), manufactured load: flexible CG with the
+    tensor-core preconditioner reaches the FP64 solution."""
+    pi = np.pi
+    prob = STProblem(3, 4, 32)
+    s = lambda x: np.sin(pi * x)
+    F = prob.load_separable([(1.0, np.cos, [s, s, s]), (3 * pi ** 2, np.sin, [s, s, s])])
+    Fg = torch.from_numpy(F).cuda()
+    S64 = _solver(3, 4, 32)
+    u64, i64 = S64.solve(Fg, tol=1e-12, maxit=300)
+    Sm = _solver(3, 4, 32, precision=form)
+    u8, i8 = Sm.solve(Fg, tol=1e-8, maxit=300)
+    assert i8[0]["status"] == "ok" and i8[0]["true_rel_res"] <= 1.5e-8
+    assert i8[0]["iters"] <= 2 * 12 + 4
+    u12, i12 = Sm.solve(Fg, tol=1e-12, maxit=300)
+    assert i12[0]["status"] == "ok"
+    assert _rel(u12.cpu().numpy(), u64.cpu().numpy()) <= 1e-8
+    print(form, "iters@1e-8", i8[0]["iters"], "iters@1e-12", i12[0]["iters"], "fp64 iters@1e-12", i64[0]["iters"])
+
+
+def test_mixed_solve_cfg4_bf16():
+    prob_N = 18125250
+    S = _solver(3, 3, 64, precision="bf16")
+    F = torch.from_numpy(synth.uniform(prob_N, 4)).cuda()
+    u, info = S.solve(F, tol=1e-8, maxit=200)
+    assert info[0]["status"] == "ok" and info[0]["true_rel_res"] <= 1.5e-8
+    assert info[0]["iters"] <= 40
