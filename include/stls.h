@@ -159,6 +159,40 @@ long long stls_launch_count(const stls_ctx *ctx);
 int stls_enable_timing(stls_ctx *ctx, int on);
 int stls_phase_times(stls_ctx *ctx, double *ms_out3, long long *count_out3);
 
+/* ---- allocation-free preconditioner apply ------------------------------------
+ * The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate device memory when they need the preconditioner: work being
+ * recorded into a CUDA graph under stream capture (cudaMalloc cannot be
+ * captured), real-time loops that cannot afford the allocator's latency or
+ * its device synchronization, and plugin hosts that forbid allocation.
+ * Such callers cannot create a context either (stls_create allocates), so
+ * every input comes from the caller.
+ *
+ * Computes z = P^{-1} r in FP64 exactly as stls_apply_precond does in the
+ * STLS_FP64 form (the same mode products and eigenvalue division), with the
+ * two intermediate tensors held in a fixed 8 MiB device array inside the
+ * library, which every GPU that loads the library keeps until process exit.
+ *   d        spatial dimension 1..3
+ *   n        host array of d+1 sizes: n_1..n_d, n_t (each 1..128)
+ *   batch    right-hand sides; batch * prod(n) must not exceed 524288,
+ *            otherwise STLS_EINVAL is returned and nothing is launched
+ *   U        host array of d+1 DEVICE pointers to the eigenvector matrices
+ *            U_1..U_d, U_t (row-major n_k x n_k, U^T M U = I), e.g. uploads of
+ *            stls_host_factor(..., STLS_F_EIGVEC, k, ...)
+ *   lam      host array of d+1 DEVICE pointers to the eigenvalues (length n_k)
+ *   r, z     DEVICE, batch x N, colexicographic; r == z is allowed
+ *   stream   cudaStream_t (NULL = legacy default stream)
+ * Nothing is allocated or freed.  The first call on a device looks up the
+ * array's device address with cudaGetSymbolAddress (with that device
+ * current); make that first call outside any stream capture.  All calls share
+ * the array and nothing in it needs to start at zero; calls whose kernels
+ * overlap on the GPU (different streams or threads) race on it and must be
+ * serialized by the caller.  Errors: STLS_EINVAL (sizes, NULL pointers),
+ * STLS_ECUDA (lookup or launch failure); text via stls_last_error(NULL). */
+int stls_apply_precond_noalloc(int d, const int *n, int batch, const double *const *U,
+                               const double *const *lam, const double *r, double *z,
+                               void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

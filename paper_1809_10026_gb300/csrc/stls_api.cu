@@ -388,6 +388,11 @@ int solve_impl(stls_ctx *c, const double *F, double *u, double tol, int maxit, s
 
 }  // namespace
 
+namespace stls {
+// Error text for context-free calls, read back with stls_last_error(NULL).
+void set_thread_error(const std::string &msg) { g_create_error = msg; }
+}  // namespace stls
+
 // ---- C ABI ----------------------------------------------------------------------------
 extern "C" {
 
