@@ -1,5 +1,5 @@
 // Tensor-core fast-diagonalization solve (Algorithm 1, steps 2-4) for the
-// mixed-precision form, sm_103a (tcgen05).
+// mixed-precision form, sm_103a (tcgen05 + bulk TMA copies).
 //
 // Each of the 2(d+1) mode products is one launch of a persistent kernel that
 // computes, for tiles of 128 fibers of the mode-k unfolding,
@@ -7,23 +7,30 @@
 // with tcgen05.mma: A = the fiber tile (M = 128, K = n_k padded), B = W
 // (N = n_k padded to 16, K-major), D = FP32 accumulators in tensor memory
 // (TMEM lane = fiber, column = output index m).  Operands are BF16 (kind::f16)
-// or TF32 (kind::tf32).  Both operands use the canonical no-swizzle K-major
-// shared-memory layout: 8-row x 16-byte core matrices, 8-row groups 128 B
-// apart (SBO) and 16-byte K chunks LBO apart.  Each thread owns one fiber: it
-// gathers the fiber's K values with coalesced loads across the warp (32
-// consecutive fibers per k), converts them, and stores 16-byte chunks.  The
-// epilogue reads its warp's 32 TMEM lanes with tcgen05.ld and writes each
-// output index m for 32 consecutive fibers (coalesced).
+// or TF32 (kind::tf32), in the canonical no-swizzle K-major shared-memory
+// layout: 8-row x 16-byte core matrices, 8-row groups 128 B apart (SBO), and
+// 16-byte K chunks LBO apart.
+//
+// Layout rotation.  The tensor is stored with one mode fastest; the pass for
+// mode k reads it with mode k fastest, so a fiber is n_k contiguous entries
+// and a tile of 128 fibers is one contiguous block, fetched by a single
+// cp.async.bulk into shared memory (double-buffered, completion tracked by an
+// mbarrier transaction count).  The pass writes its output with mode k
+// slowest: entry (m, f) goes to m * (N / n_k) + f, which is the layout with
+// mode k+1 fastest, and for each m a warp stores 32 consecutive fibers.  The
+// first pass reads r in its natural order (mode 1 fastest); after 2(d+1)
+// passes the order is natural again and the last pass writes z.
 //
 // The first pass reads FP64 r, the last writes FP64 z; the 2d intermediate
 // tensors are BF16 (kind::f16) or FP32 (kind::tf32).  The division by the
 // eigenvalue sum lambda_t[i_t] + sum_k lambda_k[i_k] (step 3) is fused into
-// the epilogue of the forward time product, in FP32 from the FP64
+// the epilogue of the forward time product, whose fibers are exactly the
+// colexicographic spatial indices; it is done in FP32 from the FP64
 // eigenvalues rounded once.
 //
 // Every wait on an mbarrier is bounded: on timeout the kernel records an
 // error code in host-mapped memory, waits once more (bounded) for its own
-// MMAs, frees its tensor memory and returns.
+// copies and MMAs, frees its tensor memory and returns.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -41,7 +48,8 @@ constexpr int kFib = 128;      // fibers per tile = MMA M = TMEM lanes
 constexpr int kThreads = 128;  // warp w owns TMEM lanes 32w .. 32w+31
 constexpr uint32_t kTmemCols = 128;
 constexpr uint32_t kSpinLimit = 1u << 24;
-constexpr int kBlocksPerSM = 4;  // 4 x 128 TMEM columns = 512 per SM
+constexpr int kMaxBlocksPerSM = 4;  // 4 x 128 TMEM columns = 512 per SM
+constexpr int kSmemPerSM = 227 * 1024;
 
 enum { KIND_BF16 = 0, KIND_TF32 = 1 };
 
@@ -49,18 +57,18 @@ struct TcPass {
   const void *in;
   void *out;
   const uint8_t *bimg;  // canonical smem image of W (B operand)
-  long long nfib;       // fibers = outer * inner
-  long long inner;
-  long long in_stride;   // elements between consecutive outer slabs (input)
-  long long out_stride;  // same for the output
-  int n, kp, np;         // mode size, padded K, padded N
-  int bytes_a, bytes_b;  // smem bytes reserved for the A tile and the B operand
-  int bytes_bimg;        // bytes of the B image copied in
+  long long nfib;       // fibers in the batch = B * N / n
+  long long fib_per_b;  // N / n
+  long long N;          // entries per right-hand side
+  int n, kp, np;        // mode size, padded K, padded N
+  int bytes_raw;        // one raw input tile: 128 * n * sizeof(InT)
+  int bytes_a, bytes_b; // A tile and B image in shared memory
+  int bulk;             // 1: input 16-byte aligned, full tiles use bulk copies
   uint32_t idesc;
-  uint32_t lbo_b;        // K-chunk stride of the B image
-  const float *lam_t;    // division (forward time pass only)
+  uint32_t lbo_b;       // K-chunk stride of the B image
+  const float *lam_t;   // division (forward time pass only)
   const float *lam_s;
-  int *err;              // host-mapped error word
+  int *err;             // host-mapped error word
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -105,6 +113,16 @@ __device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
   return false;
 }
 
+// One bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned)
+// from global to shared memory, completing a transaction on `mbar`.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(mbar)
+      : "memory");
+}
+
 __device__ __forceinline__ float to_f32(double v) { return static_cast<float>(v); }
 __device__ __forceinline__ float to_f32(float v) { return v; }
 __device__ __forceinline__ float to_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
@@ -131,22 +149,37 @@ __global__ void __launch_bounds__(kThreads) tc_modeprod_kernel(TcPass a) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ uint32_t tmem_holder;
   __shared__ int flag_ok;
-  __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t mbar_mma;
+  __shared__ __align__(8) uint64_t mbar_load[2];
   const int tid = threadIdx.x, warp = tid >> 5;
-  uint8_t *sA = smem;
-  uint8_t *sB = smem + a.bytes_a;
-  const uint32_t mbar_addr = smem_u32(&mbar);
+  uint8_t *sA = smem + 2 * a.bytes_raw;
+  uint8_t *sB = sA + a.bytes_a;
+  const uint32_t mma_bar = smem_u32(&mbar_mma);
+  const uint32_t load_bar0 = smem_u32(&mbar_load[0]);  // stage s uses load_bar0 + 8 s
+  const uint32_t raw0 = smem_u32(smem);                // stage s uses raw0 + s * bytes_raw
+  const long long ntiles = (a.nfib + kFib - 1) / kFib;
+  const long long nfull = a.bulk ? a.nfib / kFib : 0;  // tiles fetched by bulk copies
+  const InT *in = static_cast<const InT *>(a.in);
 
-  // B operand image (already in canonical layout) -> shared memory
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mma_bar));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(load_bar0));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(load_bar0 + 8));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    asm volatile("fence.proxy.async.shared::cta;");
+    flag_ok = 1;
+    // prefetch this CTA's first two tiles
+    for (int i = 0; i < 2; ++i) {
+      const long long t = blockIdx.x + static_cast<long long>(i) * gridDim.x;
+      if (t < nfull)
+        bulk_load(raw0 + i * a.bytes_raw, in + t * kFib * a.n, static_cast<uint32_t>(a.bytes_raw),
+                  load_bar0 + 8 * i);
+    }
+  }
   {
     const uint4 *src = reinterpret_cast<const uint4 *>(a.bimg);
     uint4 *dst = reinterpret_cast<uint4 *>(sB);
-    for (int i = tid; i < a.bytes_bimg / 16; i += kThreads) dst[i] = src[i];
-  }
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar_addr));
-    asm volatile("fence.mbarrier_init.release.cluster;");
-    flag_ok = 1;
+    for (int i = tid; i < a.bytes_b / 16; i += kThreads) dst[i] = src[i];
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -161,31 +194,33 @@ __global__ void __launch_bounds__(kThreads) tc_modeprod_kernel(TcPass a) {
   const uint32_t tmem = tmem_holder;
 
   constexpr int esz = KIND == KIND_BF16 ? 2 : 4;
-  constexpr int kcw = 16 / esz;               // K values per 16-byte chunk
+  constexpr int kcw = 16 / esz;                      // K values per 16-byte chunk
   constexpr int kstep = KIND == KIND_BF16 ? 16 : 8;  // K per MMA instruction
   const int nchunk = a.kp / kcw;
-  const uint32_t lbo_a = (kFib / 8) * 128;    // 2048 B between K chunks of the A tile
+  const uint32_t lbo_a = (kFib / 8) * 128;  // 2048 B between K chunks of the A tile
   const uint32_t sA_addr = smem_u32(sA), sB_addr = smem_u32(sB);
-  const long long ntiles = (a.nfib + kFib - 1) / kFib;
-  uint32_t phase = 0;
+  uint32_t mma_phase = 0;
 
-  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const long long f = tile * kFib + tid;
-    const bool valid = f < a.nfib;
-    long long o = 0, c = 0;
-    if (valid) {
-      o = f / a.inner;
-      c = f - o * a.inner;
+  int i = 0;
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+    const int s = i & 1;
+    const bool full = t < nfull;
+    if (full) {
+      if (!mbar_wait(load_bar0 + 8 * s, static_cast<uint32_t>((i >> 1) & 1))) flag_ok = 0;
     }
-    const InT *src = static_cast<const InT *>(a.in) + o * a.in_stride + c;
-    // gather this fiber's K values into 16-byte chunks of the canonical layout
+    __syncthreads();
+    if (!flag_ok) break;
+    const long long f = t * kFib + tid;
+    const bool valid = f < a.nfib;
+    const InT *src = full ? reinterpret_cast<const InT *>(smem + s * a.bytes_raw) + tid * a.n : in + f * a.n;
+    // this fiber's K values -> 16-byte chunks of the canonical layout
     uint8_t *rowp = sA + (tid >> 3) * 128 + (tid & 7) * 16;
     for (int ch = 0; ch < nchunk; ++ch) {
       float v[8];
 #pragma unroll
       for (int j = 0; j < kcw; ++j) {
         const int k = ch * kcw + j;
-        v[j] = (valid && k < a.n) ? to_f32(src[static_cast<long long>(k) * a.inner]) : 0.f;
+        v[j] = (valid && k < a.n) ? to_f32(src[k]) : 0.f;
       }
       uint4 pk;
       if (KIND == KIND_BF16) {
@@ -205,30 +240,41 @@ __global__ void __launch_bounds__(kThreads) tc_modeprod_kernel(TcPass a) {
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     if (tid == 0) {
+      // raw[s] is free again: fetch the tile two steps ahead
+      const long long t2 = t + 2LL * gridDim.x;
+      if (t2 < nfull)
+        bulk_load(raw0 + s * a.bytes_raw, in + t2 * kFib * a.n, static_cast<uint32_t>(a.bytes_raw),
+                  load_bar0 + 8 * s);
       asm volatile("tcgen05.fence::after_thread_sync;");
       const int nsteps = a.kp / kstep;
-      for (int s = 0; s < nsteps; ++s) {
+      for (int st = 0; st < nsteps; ++st) {
         // one instruction consumes two 16-byte K chunks
-        const uint64_t ad = make_desc(sA_addr + 2 * s * lbo_a, lbo_a, 128);
-        const uint64_t bd = make_desc(sB_addr + 2 * s * a.lbo_b, a.lbo_b, 128);
-        mma_issue(tmem, ad, bd, a.idesc, s > 0 ? 1u : 0u, KIND);
+        const uint64_t ad = make_desc(sA_addr + 2 * st * lbo_a, lbo_a, 128);
+        const uint64_t bd = make_desc(sB_addr + 2 * st * a.lbo_b, a.lbo_b, 128);
+        mma_issue(tmem, ad, bd, a.idesc, st > 0 ? 1u : 0u, KIND);
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                       mbar_addr)
+                       mma_bar)
                    : "memory");
-      if (!mbar_wait(mbar_addr, phase)) {
+      if (!mbar_wait(mma_bar, mma_phase)) {
         *reinterpret_cast<volatile int *>(a.err) = 1;
-        mbar_wait(mbar_addr, phase);  // give in-flight MMAs one more bounded chance
+        mbar_wait(mma_bar, mma_phase);  // give in-flight MMAs one more bounded chance
         flag_ok = 0;
       }
     }
-    phase ^= 1u;
+    mma_phase ^= 1u;
     __syncthreads();
     if (!flag_ok) break;
     asm volatile("tcgen05.fence::after_thread_sync;");
-    // epilogue: TMEM lane = fiber (this thread), columns = output index m
-    OutT *dst = static_cast<OutT *>(a.out) + o * a.out_stride + c;
-    const float lam_c = (DIVIDE && valid) ? a.lam_s[c] : 0.f;
+    // epilogue: TMEM lane = fiber (this thread), columns = output index m;
+    // entry (m, fiber) goes to m * (N / n) + fiber within its right-hand side
+    long long b = 0, fl = 0;
+    if (valid) {
+      b = f / a.fib_per_b;
+      fl = f - b * a.fib_per_b;
+    }
+    OutT *dst = static_cast<OutT *>(a.out) + b * a.N + fl;
+    const float lam_c = (DIVIDE && valid) ? a.lam_s[fl] : 0.f;
     for (int cb = 0; cb < a.np / 16; ++cb) {
       uint32_t r[16];
       const uint32_t taddr = tmem + (static_cast<uint32_t>(warp * 32) << 16) + cb * 16;
@@ -247,10 +293,18 @@ __global__ void __launch_bounds__(kThreads) tc_modeprod_kernel(TcPass a) {
           if (m < a.n) {
             float val = __uint_as_float(r[j]);
             if (DIVIDE) val = val / (a.lam_t[m] + lam_c);
-            store_out(dst + static_cast<long long>(m) * a.inner, val);
+            store_out(dst + static_cast<long long>(m) * a.fib_per_b, val);
           }
         }
       }
+    }
+  }
+  if (!flag_ok && tid == 0) {
+    *reinterpret_cast<volatile int *>(a.err) = 1;
+    // let this CTA's outstanding bulk copies land before its shared memory goes away
+    for (int k = 0; k < 2; ++k) {
+      const long long t = blockIdx.x + static_cast<long long>(i + k) * gridDim.x;
+      if (t < nfull) mbar_wait(load_bar0 + 8 * ((i + k) & 1), static_cast<uint32_t>(((i + k) >> 1) & 1));
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -264,7 +318,7 @@ __global__ void __launch_bounds__(kThreads) tc_modeprod_kernel(TcPass a) {
 struct Mode {
   int n, kp, np;
   uint8_t *bimg_fwd, *bimg_bwd;
-  int bytes_a, bytes_b, bytes_bimg;
+  int bytes_a, bytes_b;
   uint32_t lbo_b;
 };
 
@@ -313,16 +367,21 @@ std::vector<uint8_t> b_image(const std::vector<double> &W, int n, int np, int kp
 }
 
 template <typename InT, typename OutT, int KIND, bool DIVIDE>
-cudaError_t launch_pass(const TcPass &p, int sms, cudaStream_t s) {
-  const size_t smem = static_cast<size_t>(p.bytes_a) + p.bytes_b;
+cudaError_t launch_pass(TcPass p, int sms, cudaStream_t s) {
+  p.bytes_raw = kFib * p.n * static_cast<int>(sizeof(InT));
+  p.bulk = (reinterpret_cast<uintptr_t>(p.in) % 16 == 0) ? 1 : 0;
+  if (2 * static_cast<size_t>(p.bytes_raw) + p.bytes_a + p.bytes_b + 1024 > static_cast<size_t>(kSmemPerSM)) {
+    p.bulk = 0;  // two raw stages do not fit: every tile is gathered with direct loads
+  }
+  if (!p.bulk) p.bytes_raw = 0;
+  const size_t smem = 2 * static_cast<size_t>(p.bytes_raw) + p.bytes_a + p.bytes_b;
   auto kern = tc_modeprod_kernel<InT, OutT, KIND, DIVIDE>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   const long long ntiles = (p.nfib + kFib - 1) / kFib;
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
-  if (e != cudaSuccess) return e;
-  if (per_sm > kBlocksPerSM) per_sm = kBlocksPerSM;
+  // resident CTAs per SM from the shared-memory budget (1 KB reserved per CTA)
+  int per_sm = static_cast<int>(kSmemPerSM / (smem + 1024 + 64));
+  if (per_sm > kMaxBlocksPerSM) per_sm = kMaxBlocksPerSM;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   long long grid = static_cast<long long>(sms) * per_sm;
   if (grid > ntiles) grid = ntiles;
@@ -382,14 +441,8 @@ cudaError_t tc_fd_create(TcFd &tc, int precision, int d, const int *n, int B,
     const int esz = kind == KIND_BF16 ? 2 : 4, kcw = 16 / esz;
     m.lbo_b = static_cast<uint32_t>(m.np / 8) * 128;
     const int nch = m.kp / kcw;
-    m.bytes_bimg = nch * static_cast<int>(m.lbo_b);
-    // Reserve enough shared memory that the operand extents stay inside the
-    // allocation under either assignment of the two core-matrix strides.
-    const int lbo_a = (kFib / 8) * 128;
-    m.bytes_a = std::max(nch * lbo_a, (kFib / 8 - 1) * lbo_a + nch * 128);
-    m.bytes_b = std::max(m.bytes_bimg, (m.np / 8 - 1) * static_cast<int>(m.lbo_b) + nch * 128);
-    m.bytes_a = (m.bytes_a + 127) / 128 * 128;
-    m.bytes_b = (m.bytes_b + 127) / 128 * 128;
+    m.bytes_b = nch * static_cast<int>(m.lbo_b);
+    m.bytes_a = nch * (kFib / 8) * 128;
     std::vector<uint8_t> fwd = b_image(U[k], m.n, m.np, m.kp, kind, true);   // W = U^T
     std::vector<uint8_t> bwd = b_image(U[k], m.n, m.np, m.kp, kind, false);  // W = U
     if ((e = dev_alloc(tc, &m.bimg_fwd, fwd.size())) != cudaSuccess) return e;
@@ -434,18 +487,14 @@ cudaError_t tc_fd_apply(TcFd &tc, const double *r, double *z, cudaStream_t s) {
     p.in = st == 0 ? static_cast<const void *>(r) : im->inter[(st - 1) % 2];
     p.out = st == nprod - 1 ? static_cast<void *>(z) : im->inter[st % 2];
     p.bimg = fwd ? m.bimg_fwd : m.bimg_bwd;
-    long long inner = 1;
-    for (int l = 0; l < k && l < d; ++l) inner *= tc.n[l];
-    const long long slab = static_cast<long long>(m.n) * inner;
-    p.inner = inner;
-    p.in_stride = p.out_stride = slab;
-    p.nfib = static_cast<long long>(tc.B) * tc.N / m.n;
+    p.N = tc.N;
+    p.fib_per_b = tc.N / m.n;
+    p.nfib = static_cast<long long>(tc.B) * p.fib_per_b;
     p.n = m.n;
     p.kp = m.kp;
     p.np = m.np;
     p.bytes_a = m.bytes_a;
     p.bytes_b = m.bytes_b;
-    p.bytes_bimg = m.bytes_bimg;
     p.lbo_b = m.lbo_b;
     p.idesc = make_idesc(kind, kFib, m.np);
     p.lam_t = im->lam_t;
