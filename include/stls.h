@@ -66,13 +66,23 @@ typedef struct {
   int batch;        /* right-hand sides per call, 1..1024 */
   int time_pencil;  /* 0: time pencil (M_t, K_t) on [0,T]; 1: parametric (T = 1)
                        pencil of Eq. preconditioner.  Equal when T = 1. */
+  int refine;       /* mixed forms only.  0: flexible CG in FP64 with the
+                       tensor-core preconditioner.  1: iterative refinement:
+                       an outer loop computes the residual r = F - A u in FP64
+                       and corrects u with an inner flexible CG in FP32
+                       (FP32 vectors and A p, tensor-core preconditioner, inner
+                       products accumulated in FP64) that reduces its scaled
+                       residual by inner_tol. */
+  double inner_tol; /* relative tolerance of the inner solves (0: 1e-4) */
 } stls_params;
 
 typedef struct {
-  int iters;            /* CG iterations performed */
+  int iters;            /* CG iterations performed (inner iterations when refine = 1) */
   int status;           /* STLS_OK, STLS_ENOTCONV, STLS_EBREAKDOWN or STLS_ENONFINITE */
-  double rel_res;       /* ||r_k|| / ||F|| of the recursively updated residual */
+  double rel_res;       /* ||r_k|| / ||F|| of the residual the stopping test used:
+                           recursively updated (refine = 0) or F - A u in FP64 (refine = 1) */
   double true_rel_res;  /* ||F - A u|| / ||F|| recomputed in FP64 at exit */
+  int outer;            /* FP64 residual evaluations of the refinement loop (0 if refine = 0) */
 } stls_solve_info;
 
 /* Create a solver context: builds the 1D Galerkin matrices (Sec. 4.1-4.2) and
@@ -107,7 +117,9 @@ int stls_apply_precond(stls_ctx *ctx, const double *r, double *z);
 
 /* Solve A u = F for the batch by (flexible) preconditioned CG from u = 0,
  * stopping each right-hand side when ||r_k|| / ||F|| <= tol (Sec. 5: tolerance
- * on the relative residual, zero initial guess).  F, u: device, B x N.
+ * on the relative residual, zero initial guess).  With refine = 1, maxit bounds
+ * the total inner iterations and the test uses the FP64 residual F - A u.
+ * F, u: device, B x N.
  * info: host array of B entries (may be NULL).  Returns STLS_OK if every
  * right-hand side converged, else the first non-OK per-RHS status. */
 int stls_solve(stls_ctx *ctx, const double *F, double *u, double tol, int maxit,
@@ -154,10 +166,11 @@ long long stls_launch_count(const stls_ctx *ctx);
 
 /* Per-phase device timing of solves.  When enabled, stls_solve records CUDA
  * events around each phase; stls_phase_times returns, for phase ids
- * 0 = A x, 1 = P^{-1} r, 2 = CG vector updates and reductions, the summed
- * milliseconds and the number of executions since the last reset. */
+ * 0 = A x in FP64, 1 = P^{-1} r, 2 = CG vector updates and reductions,
+ * 3 = A x in FP32 (refinement form), the summed milliseconds and the number
+ * of executions since the last reset (arrays of 4). */
 int stls_enable_timing(stls_ctx *ctx, int on);
-int stls_phase_times(stls_ctx *ctx, double *ms_out3, long long *count_out3);
+int stls_phase_times(stls_ctx *ctx, double *ms_out4, long long *count_out4);
 
 /* ---- allocation-free preconditioner apply ------------------------------------
  * The paper has no counterpart to this entry point; it serves callers that

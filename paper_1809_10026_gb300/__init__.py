@@ -40,20 +40,22 @@ class Solver:
     """Solver context for (0,1)^d x (0,T) with degree p splines and n_el elements.
 
     precision: "fp64" or the mixed forms "tf32" / "bf16" (tensor-core FD
-    mode products, FP64 elsewhere).  Vectors are float64 CUDA tensors of
+    mode products, FP64 elsewhere).  refine=True (mixed forms) solves by
+    iterative refinement: FP64 residuals F - A u, inner FP32 flexible CG.  Vectors are float64 CUDA tensors of
     shape (batch, N) or (N,) for batch 1, in colexicographic order
     (direction 1 fastest, time slowest).
     """
 
     def __init__(self, d, p, n_el, T=1.0, precision="fp64", flexible=None, batch=1, p_t=None,
-                 n_el_t=None, time_pencil="physical", device=None):
+                 n_el_t=None, time_pencil="physical", device=None, refine=False, inner_tol=0.0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("stls.Solver needs a CUDA device (no CPU fallback)")
         self.torch = torch
         self.device = torch.device("cuda" if device is None else device)
         self.lib = _lib.load()
-        self.params = make_params(d, p, n_el, T, precision, flexible, batch, p_t, n_el_t, time_pencil)
+        self.params = make_params(d, p, n_el, T, precision, flexible, batch, p_t, n_el_t, time_pencil,
+                                  refine, inner_tol)
         self.ctx = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             stream = torch.cuda.current_stream(self.device).cuda_stream
@@ -171,11 +173,11 @@ class Solver:
         _check(self.lib.stls_enable_timing(self.ctx, int(on)), self.ctx)
 
     def phase_times(self):
-        ms = (ctypes.c_double * 3)()
-        cnt = (ctypes.c_longlong * 3)()
+        ms = (ctypes.c_double * 4)()
+        cnt = (ctypes.c_longlong * 4)()
         _check(self.lib.stls_phase_times(self.ctx, ms, cnt), self.ctx)
-        names = ["apply_A", "precond", "cg_vectors"]
-        return {names[i]: (ms[i], cnt[i]) for i in range(3)}
+        names = ["apply_A", "precond", "cg_vectors", "apply_A_f32"]
+        return {names[i]: (ms[i], cnt[i]) for i in range(4)}
 
     def close(self):
         if getattr(self, "ctx", None) and self.ctx.value:

@@ -21,16 +21,16 @@ class Params(ctypes.Structure):
     _fields_ = [("d", ctypes.c_int), ("p_s", ctypes.c_int), ("p_t", ctypes.c_int),
                 ("n_el_s", ctypes.c_int * 3), ("n_el_t", ctypes.c_int), ("T", ctypes.c_double),
                 ("precision", ctypes.c_int), ("flexible", ctypes.c_int), ("batch", ctypes.c_int),
-                ("time_pencil", ctypes.c_int)]
+                ("time_pencil", ctypes.c_int), ("refine", ctypes.c_int), ("inner_tol", ctypes.c_double)]
 
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("status", ctypes.c_int), ("rel_res", ctypes.c_double),
-                ("true_rel_res", ctypes.c_double)]
+                ("true_rel_res", ctypes.c_double), ("outer", ctypes.c_int)]
 
     def as_dict(self):
         return {"iters": self.iters, "status": STATUS_NAMES.get(self.status, str(self.status)),
-                "rel_res": self.rel_res, "true_rel_res": self.true_rel_res}
+                "rel_res": self.rel_res, "true_rel_res": self.true_rel_res, "outer": self.outer}
 
 
 _lib = None
@@ -75,7 +75,7 @@ def load():
 
 
 def make_params(d, p, n_el, T=1.0, precision="fp64", flexible=None, batch=1, p_t=None, n_el_t=None,
-                time_pencil="physical"):
+                time_pencil="physical", refine=False, inner_tol=0.0):
     n_el_s = [int(n_el)] * d if isinstance(n_el, int) else [int(v) for v in n_el]
     if len(n_el_s) != d:
         raise ValueError("n_el must be an int or a list of d ints")
@@ -91,4 +91,6 @@ def make_params(d, p, n_el, T=1.0, precision="fp64", flexible=None, batch=1, p_t
     prm.flexible = int(precision != "fp64") if flexible is None else int(flexible)
     prm.batch = batch
     prm.time_pencil = {"physical": 0, "hat": 1}[time_pencil]
+    prm.refine = int(bool(refine))
+    prm.inner_tol = float(inner_tol)
     return prm

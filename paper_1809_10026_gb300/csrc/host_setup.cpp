@@ -34,6 +34,9 @@ std::string validate_params(const stls_params &prm) {
   if (prm.batch < 1 || prm.batch > 1024) return "batch must be in [1, 1024]";
   if (prm.flexible != 0 && prm.flexible != 1) return "flexible must be 0 or 1";
   if (prm.time_pencil != 0 && prm.time_pencil != 1) return "time_pencil must be 0 or 1";
+  if (prm.refine != 0 && prm.refine != 1) return "refine must be 0 or 1";
+  if (prm.refine == 1 && prm.precision == STLS_FP64) return "refine = 1 needs a mixed precision form";
+  if (!(prm.inner_tol >= 0.0) || !(prm.inner_tol < 1.0)) return "inner_tol must be in [0, 1)";
   return "";
 }
 

@@ -1,4 +1,6 @@
-// Banded FP64 mode products for the matrix-free system matrix (Eq. A_kron).
+// Banded mode products for the matrix-free system matrix (Eq. A_kron), in
+// FP64 (the solver's residuals) or FP32 (the inner solves of the refinement
+// form).
 //
 // One launch applies up to 8 terms out[t.out] += t.scale * (t.band x_k in[t.in])
 // along one mode, where every band is a 1D Galerkin matrix of half-width p
@@ -16,10 +18,11 @@ constexpr int kTC = 32;
 constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
 
-template <int RPT>
+template <typename T, int RPT>
 __global__ void __launch_bounds__(kThreads)
-    banded_f64_kernel(BandSpec spec, ModeView v, long long ncols) {
-  extern __shared__ double sm[];
+    banded_kernel(BandSpecT<T> spec, ModeView v, long long ncols) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  T *sm = reinterpret_cast<T *>(sm_raw);
   const int n = v.n, p = spec.p, w = 2 * p + 1;
   const int rows_pad = n + 2 * p;
   const int ntile = spec.n_in > spec.n_out ? spec.n_in : spec.n_out;
@@ -27,14 +30,14 @@ __global__ void __launch_bounds__(kThreads)
   const int ncol_tile = static_cast<int>(min(static_cast<long long>(kTC), ncols - col0));
   const bool linear = v.inner == 1 && v.in_outer_stride == n;
   for (int t = 0; t < spec.n_in; ++t) {
-    double *Xs = sm + static_cast<size_t>(t) * rows_pad * kTC;
-    const double *src = spec.in[t];
+    T *Xs = sm + static_cast<size_t>(t) * rows_pad * kTC;
+    const T *src = spec.in[t];
     for (int e = threadIdx.x; e < p * kTC; e += kThreads) {
       Xs[e] = 0.0;
       Xs[(n + p) * kTC + e] = 0.0;
     }
     if (linear) {
-      const double *s0 = src + col0 * n;
+      const T *s0 = src + col0 * n;
       for (int e = threadIdx.x; e < ncol_tile * n; e += kThreads) {
         int cc = e / n, j = e - cc * n;
         Xs[(j + p) * kTC + cc] = s0[e];
@@ -46,7 +49,7 @@ __global__ void __launch_bounds__(kThreads)
     } else {
       for (int e = threadIdx.x; e < n * kTC; e += kThreads) {
         int j = e / kTC, cc = e - j * kTC;
-        double val = 0.0;
+        T val = T(0);
         if (cc < ncol_tile) {
           long long col = col0 + cc;
           long long o = col / v.inner, c = col - o * v.inner;
@@ -58,20 +61,20 @@ __global__ void __launch_bounds__(kThreads)
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double acc[RPT][kMaxBandOut];
+  T acc[RPT][kMaxBandOut];
 #pragma unroll
   for (int r = 0; r < RPT; ++r)
 #pragma unroll
-    for (int o = 0; o < kMaxBandOut; ++o) acc[r][o] = 0.0;
+    for (int o = 0; o < kMaxBandOut; ++o) acc[r][o] = T(0);
 #pragma unroll
   for (int r = 0; r < RPT; ++r) {
     const int i = warp + kWarps * r;
     if (i < n) {
       for (int t = 0; t < spec.n_terms; ++t) {
-        const BandTerm tm = spec.term[t];
-        const double *Xs = sm + static_cast<size_t>(tm.in) * rows_pad * kTC + lane;
-        const double *bnd = tm.band + static_cast<size_t>(i) * w;
-        double s = 0.0;
+        const BandTermT<T> tm = spec.term[t];
+        const T *Xs = sm + static_cast<size_t>(tm.in) * rows_pad * kTC + lane;
+        const T *bnd = tm.band + static_cast<size_t>(i) * w;
+        T s = T(0);
         for (int o = 0; o < w; ++o) s = fma(__ldg(bnd + o), Xs[(i + o) * kTC], s);
 #pragma unroll
         for (int q = 0; q < kMaxBandOut; ++q)
@@ -93,10 +96,10 @@ __global__ void __launch_bounds__(kThreads)
   (void)ntile;
   const bool linear_out = v.inner == 1 && v.out_outer_stride == n && spec.last_add == nullptr;
   for (int q = 0; q < spec.n_out; ++q) {
-    const double *Os = sm + static_cast<size_t>(q) * rows_pad * kTC;
-    double *dst = spec.out[q];
+    const T *Os = sm + static_cast<size_t>(q) * rows_pad * kTC;
+    T *dst = spec.out[q];
     if (linear_out) {
-      double *d0 = dst + col0 * n;
+      T *d0 = dst + col0 * n;
       for (int e = threadIdx.x; e < ncol_tile * n; e += kThreads) {
         int cc = e / n, i = e - cc * n;
         d0[e] = Os[(i + p) * kTC + cc];
@@ -107,7 +110,7 @@ __global__ void __launch_bounds__(kThreads)
         if (cc >= ncol_tile) continue;
         long long col = col0 + cc;
         long long o = col / v.inner, c = col - o * v.inner;
-        double val = Os[(i + p) * kTC + cc];
+        T val = Os[(i + p) * kTC + cc];
         if (spec.last_add != nullptr && q == spec.last_out && i == n - 1) val += spec.last_add[o * v.inner + c];
         dst[o * v.out_outer_stride + static_cast<long long>(i) * v.inner + c] = val;
       }
@@ -115,23 +118,24 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
-template <int RPT>
-cudaError_t launch_rpt(const BandSpec &spec, const ModeView &v, cudaStream_t s) {
+template <typename T, int RPT>
+cudaError_t launch_rpt(const BandSpecT<T> &spec, const ModeView &v, cudaStream_t s) {
   const long long ncols = v.outer * v.inner;
   const int ntile = spec.n_in > spec.n_out ? spec.n_in : spec.n_out;
-  const size_t smem = sizeof(double) * static_cast<size_t>(ntile) * (v.n + 2 * spec.p) * kTC;
-  cudaError_t e = cudaFuncSetAttribute(banded_f64_kernel<RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  const size_t smem = sizeof(T) * static_cast<size_t>(ntile) * (v.n + 2 * spec.p) * kTC;
+  cudaError_t e = cudaFuncSetAttribute(banded_kernel<T, RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   const long long grid = (ncols + kTC - 1) / kTC;
   if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-  banded_f64_kernel<RPT><<<static_cast<unsigned>(grid), kThreads, smem, s>>>(spec, v, ncols);
+  banded_kernel<T, RPT><<<static_cast<unsigned>(grid), kThreads, smem, s>>>(spec, v, ncols);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_banded_f64(const BandSpec &spec, const ModeView &v, cudaStream_t s) {
+template <typename T>
+cudaError_t launch_banded(const BandSpecT<T> &spec, const ModeView &v, cudaStream_t s) {
   if (v.n < 1 || v.n > 128 || v.inner < 1 || v.outer < 0) return cudaErrorInvalidValue;
   if (spec.n_in < 1 || spec.n_in > kMaxBandIn || spec.n_out < 1 || spec.n_out > kMaxBandOut ||
       spec.n_terms < 1 || spec.n_terms > kMaxBandTerms || spec.p < 0)
@@ -142,15 +146,18 @@ cudaError_t launch_banded_f64(const BandSpec &spec, const ModeView &v, cudaStrea
       return cudaErrorInvalidValue;
   if (v.outer == 0) return cudaSuccess;
   switch ((v.n + kWarps - 1) / kWarps) {
-    case 1: return launch_rpt<1>(spec, v, s);
-    case 2: return launch_rpt<2>(spec, v, s);
-    case 3: return launch_rpt<3>(spec, v, s);
-    case 4: return launch_rpt<4>(spec, v, s);
-    case 5: return launch_rpt<5>(spec, v, s);
-    case 6: return launch_rpt<6>(spec, v, s);
-    case 7: return launch_rpt<7>(spec, v, s);
-    default: return launch_rpt<8>(spec, v, s);
+    case 1: return launch_rpt<T, 1>(spec, v, s);
+    case 2: return launch_rpt<T, 2>(spec, v, s);
+    case 3: return launch_rpt<T, 3>(spec, v, s);
+    case 4: return launch_rpt<T, 4>(spec, v, s);
+    case 5: return launch_rpt<T, 5>(spec, v, s);
+    case 6: return launch_rpt<T, 6>(spec, v, s);
+    case 7: return launch_rpt<T, 7>(spec, v, s);
+    default: return launch_rpt<T, 8>(spec, v, s);
   }
 }
+
+template cudaError_t launch_banded<double>(const BandSpecT<double> &, const ModeView &, cudaStream_t);
+template cudaError_t launch_banded<float>(const BandSpecT<float> &, const ModeView &, cudaStream_t);
 
 }  // namespace stls

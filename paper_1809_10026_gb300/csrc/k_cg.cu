@@ -109,15 +109,16 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
+template <typename T>
 __global__ void __launch_bounds__(kThreads)
-    cg_alpha_kernel(const double *__restrict__ p, const double *__restrict__ q, long long N,
+    cg_alpha_kernel(const T *__restrict__ p, const T *__restrict__ q, long long N,
                     CGState *st, RedWork rw) {
   const int b = blockIdx.y;
-  const double *pb = p + static_cast<size_t>(b) * N, *qb = q + static_cast<size_t>(b) * N;
+  const T *pb = p + static_cast<size_t>(b) * N, *qb = q + static_cast<size_t>(b) * N;
   double v[1] = {0.0};
   for (long long i = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x; i < N;
        i += static_cast<long long>(gridDim.x) * kThreads)
-    v[0] = fma(pb[i], qb[i], v[0]);
+    v[0] = fma(static_cast<double>(pb[i]), static_cast<double>(qb[i]), v[0]);
   double tot[1];
   if (grid_sum<1>(v, rw, b, tot) && threadIdx.x == 0) {
     CGState &s = st[b];
@@ -135,22 +136,23 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
+template <typename T>
 __global__ void __launch_bounds__(kThreads)
-    cg_xr_kernel(double *__restrict__ x, double *__restrict__ r, const double *__restrict__ p,
-                 const double *__restrict__ q, long long N, double tol, CGState *st, RedWork rw) {
+    cg_xr_kernel(T *__restrict__ x, T *__restrict__ r, const T *__restrict__ p,
+                 const T *__restrict__ q, long long N, double tol, CGState *st, RedWork rw) {
   const int b = blockIdx.y;
   const bool active = st[b].active != 0;
-  const double alpha = st[b].alpha;
-  double *xb = x + static_cast<size_t>(b) * N, *rb = r + static_cast<size_t>(b) * N;
-  const double *pb = p + static_cast<size_t>(b) * N, *qb = q + static_cast<size_t>(b) * N;
+  const T alpha = static_cast<T>(st[b].alpha);
+  T *xb = x + static_cast<size_t>(b) * N, *rb = r + static_cast<size_t>(b) * N;
+  const T *pb = p + static_cast<size_t>(b) * N, *qb = q + static_cast<size_t>(b) * N;
   double v[1] = {0.0};
   if (active) {
     for (long long i = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x; i < N;
          i += static_cast<long long>(gridDim.x) * kThreads) {
       xb[i] = fma(alpha, pb[i], xb[i]);
-      double ri = fma(-alpha, qb[i], rb[i]);
+      T ri = fma(-alpha, qb[i], rb[i]);
       rb[i] = ri;
-      v[0] = fma(ri, ri, v[0]);
+      v[0] = fma(static_cast<double>(ri), static_cast<double>(ri), v[0]);
     }
   }
   double tot[1];
@@ -169,20 +171,21 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
+template <typename T>
 __global__ void __launch_bounds__(kThreads)
-    cg_beta_kernel(const double *__restrict__ z, const double *__restrict__ r,
-                   const double *__restrict__ q, long long N, int flexible, int first, CGState *st,
+    cg_beta_kernel(const T *__restrict__ z, const T *__restrict__ r,
+                   const T *__restrict__ q, long long N, int flexible, int first, CGState *st,
                    RedWork rw) {
   const int b = blockIdx.y;
-  const double *zb = z + static_cast<size_t>(b) * N, *rb = r + static_cast<size_t>(b) * N;
-  const double *qb = q + static_cast<size_t>(b) * N;
+  const T *zb = z + static_cast<size_t>(b) * N, *rb = r + static_cast<size_t>(b) * N;
+  const T *qb = q + static_cast<size_t>(b) * N;
   const bool need_zq = flexible && !first;
   double v[2] = {0.0, 0.0};
   for (long long i = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x; i < N;
        i += static_cast<long long>(gridDim.x) * kThreads) {
-    double zi = zb[i];
-    v[0] = fma(zi, rb[i], v[0]);
-    if (need_zq) v[1] = fma(zi, qb[i], v[1]);
+    const double zi = static_cast<double>(zb[i]);
+    v[0] = fma(zi, static_cast<double>(rb[i]), v[0]);
+    if (need_zq) v[1] = fma(zi, static_cast<double>(qb[i]), v[1]);
   }
   double tot[2];
   if (grid_sum<2>(v, rw, b, tot) && threadIdx.x == 0) {
@@ -211,14 +214,15 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
+template <typename T>
 __global__ void __launch_bounds__(kThreads)
-    cg_p_kernel(const double *__restrict__ z, double *__restrict__ p, long long N, int first,
+    cg_p_kernel(const T *__restrict__ z, T *__restrict__ p, long long N, int first,
                 const CGState *st) {
   const int b = blockIdx.y;
   if (!st[b].active) return;
-  const double beta = st[b].beta;
-  const double *zb = z + static_cast<size_t>(b) * N;
-  double *pb = p + static_cast<size_t>(b) * N;
+  const T beta = static_cast<T>(st[b].beta);
+  const T *zb = z + static_cast<size_t>(b) * N;
+  T *pb = p + static_cast<size_t>(b) * N;
   for (long long i = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x; i < N;
        i += static_cast<long long>(gridDim.x) * kThreads)
     pb[i] = first ? zb[i] : fma(beta, pb[i], zb[i]);
@@ -237,6 +241,80 @@ __global__ void __launch_bounds__(kThreads)
   }
   double tot[1];
   if (grid_sum<1>(v, rw, b, tot) && threadIdx.x == 0) st[b].true_rr = tot[0];
+}
+
+// Refinement form: inner right-hand side r32 = r64 / ||r64|| (FP32), d = 0,
+// and the inner CG state for it (active where the outer solve is active).
+__global__ void __launch_bounds__(kThreads)
+    ir_start_kernel(const double *__restrict__ r64, float *__restrict__ r32, float *__restrict__ d,
+                    long long N, const CGState *outer, CGState *inner, RedWork rw) {
+  const int b = blockIdx.y;
+  const double scale = outer[b].rr > 0.0 ? 1.0 / sqrt(outer[b].rr) : 0.0;
+  const double *rb = r64 + static_cast<size_t>(b) * N;
+  float *ib = r32 + static_cast<size_t>(b) * N, *db = d + static_cast<size_t>(b) * N;
+  double v[1] = {0.0};
+  for (long long i = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x; i < N;
+       i += static_cast<long long>(gridDim.x) * kThreads) {
+    const float x = static_cast<float>(rb[i] * scale);
+    ib[i] = x;
+    db[i] = 0.f;
+    v[0] = fma(static_cast<double>(x), static_cast<double>(x), v[0]);
+  }
+  double tot[1];
+  if (grid_sum<1>(v, rw, b, tot) && threadIdx.x == 0) {
+    CGState &s = inner[b];
+    s.nF2 = tot[0];
+    s.rr = tot[0];
+    s.iters = 0;
+    s.status = 0;
+    s.rel_res = 1.0;
+    s.alpha = s.beta = s.pq = s.rz = 0.0;
+    s.active = outer[b].active && tot[0] > 0.0;
+  }
+}
+
+// u += ||r64|| d for the right-hand sides whose outer solve is active.
+__global__ void __launch_bounds__(kThreads)
+    ir_correct_kernel(double *__restrict__ u, const float *__restrict__ d, long long N, const CGState *outer) {
+  const int b = blockIdx.y;
+  if (!outer[b].active) return;
+  const double s = sqrt(outer[b].rr);
+  double *ub = u + static_cast<size_t>(b) * N;
+  const float *db = d + static_cast<size_t>(b) * N;
+  for (long long i = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x; i < N;
+       i += static_cast<long long>(gridDim.x) * kThreads)
+    ub[i] = fma(s, static_cast<double>(db[i]), ub[i]);
+}
+
+// r64 = F - A u in FP64 and the outer convergence test on ||r64|| / ||F||.
+__global__ void __launch_bounds__(kThreads)
+    ir_residual_kernel(const double *__restrict__ F, const double *__restrict__ Au, double *__restrict__ r64,
+                       long long N, double tol, CGState *outer, RedWork rw) {
+  const int b = blockIdx.y;
+  const double *Fb = F + static_cast<size_t>(b) * N, *Ab = Au + static_cast<size_t>(b) * N;
+  double *rb = r64 + static_cast<size_t>(b) * N;
+  double v[1] = {0.0};
+  for (long long i = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x; i < N;
+       i += static_cast<long long>(gridDim.x) * kThreads) {
+    const double e = Fb[i] - Ab[i];
+    rb[i] = e;
+    v[0] = fma(e, e, v[0]);
+  }
+  double tot[1];
+  if (grid_sum<1>(v, rw, b, tot) && threadIdx.x == 0) {
+    CGState &s = outer[b];
+    s.true_rr = tot[0];
+    if (!s.active) return;
+    s.iters += 1;
+    s.rr = tot[0];
+    s.rel_res = sqrt(tot[0] / s.nF2);
+    if (!isfinite(tot[0])) {
+      s.status = STLS_ENONFINITE;
+      s.active = 0;
+    } else if (s.rel_res <= tol) {
+      s.active = 0;
+    }
+  }
 }
 
 __global__ void lift_combine_kernel(const double *__restrict__ Ls, const double *__restrict__ Js,
@@ -298,24 +376,51 @@ cudaError_t launch_cg_init(const double *F, double *x, double *r, long long N, i
   cg_init_kernel<<<dim3(rw.grid, B), kThreads, 0, s>>>(F, x, r, N, st, rw);
   return cudaGetLastError();
 }
-cudaError_t launch_cg_alpha(const double *p, const double *q, long long N, int B, CGState *st,
-                            RedWork rw, cudaStream_t s) {
-  cg_alpha_kernel<<<dim3(rw.grid, B), kThreads, 0, s>>>(p, q, N, st, rw);
+template <typename T>
+cudaError_t launch_cg_alpha(const T *p, const T *q, long long N, int B, CGState *st, RedWork rw, cudaStream_t s) {
+  cg_alpha_kernel<T><<<dim3(rw.grid, B), kThreads, 0, s>>>(p, q, N, st, rw);
   return cudaGetLastError();
 }
-cudaError_t launch_cg_xr(double *x, double *r, const double *p, const double *q, long long N, int B,
-                         double tol, CGState *st, RedWork rw, cudaStream_t s) {
-  cg_xr_kernel<<<dim3(rw.grid, B), kThreads, 0, s>>>(x, r, p, q, N, tol, st, rw);
+template <typename T>
+cudaError_t launch_cg_xr(T *x, T *r, const T *p, const T *q, long long N, int B, double tol, CGState *st,
+                         RedWork rw, cudaStream_t s) {
+  cg_xr_kernel<T><<<dim3(rw.grid, B), kThreads, 0, s>>>(x, r, p, q, N, tol, st, rw);
   return cudaGetLastError();
 }
-cudaError_t launch_cg_beta(const double *z, const double *r, const double *q, long long N, int B,
-                           int flexible, int first, CGState *st, RedWork rw, cudaStream_t s) {
-  cg_beta_kernel<<<dim3(rw.grid, B), kThreads, 0, s>>>(z, r, q, N, flexible, first, st, rw);
+template <typename T>
+cudaError_t launch_cg_beta(const T *z, const T *r, const T *q, long long N, int B, int flexible, int first,
+                           CGState *st, RedWork rw, cudaStream_t s) {
+  cg_beta_kernel<T><<<dim3(rw.grid, B), kThreads, 0, s>>>(z, r, q, N, flexible, first, st, rw);
   return cudaGetLastError();
 }
-cudaError_t launch_cg_p(const double *z, double *p, long long N, int B, int first, CGState *st,
-                        cudaStream_t s) {
-  cg_p_kernel<<<dim3(grid_1d(N), B), kThreads, 0, s>>>(z, p, N, first, st);
+template <typename T>
+cudaError_t launch_cg_p(const T *z, T *p, long long N, int B, int first, CGState *st, cudaStream_t s) {
+  cg_p_kernel<T><<<dim3(grid_1d(N), B), kThreads, 0, s>>>(z, p, N, first, st);
+  return cudaGetLastError();
+}
+#define STLS_INST(T)                                                                                       \
+  template cudaError_t launch_cg_alpha<T>(const T *, const T *, long long, int, CGState *, RedWork,       \
+                                          cudaStream_t);                                                   \
+  template cudaError_t launch_cg_xr<T>(T *, T *, const T *, const T *, long long, int, double, CGState *, \
+                                       RedWork, cudaStream_t);                                             \
+  template cudaError_t launch_cg_beta<T>(const T *, const T *, const T *, long long, int, int, int,        \
+                                         CGState *, RedWork, cudaStream_t);                                \
+  template cudaError_t launch_cg_p<T>(const T *, T *, long long, int, int, CGState *, cudaStream_t);
+STLS_INST(double)
+STLS_INST(float)
+#undef STLS_INST
+cudaError_t launch_ir_start(const double *r64, float *r32, float *d, long long N, int B, const CGState *outer,
+                            CGState *inner, RedWork rw, cudaStream_t s) {
+  ir_start_kernel<<<dim3(rw.grid, B), kThreads, 0, s>>>(r64, r32, d, N, outer, inner, rw);
+  return cudaGetLastError();
+}
+cudaError_t launch_ir_correct(double *u, const float *d, long long N, int B, const CGState *outer, cudaStream_t s) {
+  ir_correct_kernel<<<dim3(grid_1d(N), B), kThreads, 0, s>>>(u, d, N, outer);
+  return cudaGetLastError();
+}
+cudaError_t launch_ir_residual(const double *F, const double *Au, double *r64, long long N, int B, double tol,
+                               CGState *outer, RedWork rw, cudaStream_t s) {
+  ir_residual_kernel<<<dim3(rw.grid, B), kThreads, 0, s>>>(F, Au, r64, N, tol, outer, rw);
   return cudaGetLastError();
 }
 cudaError_t launch_true_residual(const double *F, const double *Ax, long long N, int B, CGState *st,

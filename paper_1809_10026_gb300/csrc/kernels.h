@@ -25,23 +25,31 @@ struct ModeView {
 cudaError_t launch_modeprod_f64(const double *in, double *out, const double *W, const ModeView &v,
                                 const double *lam_row, const double *lam_col, cudaStream_t s);
 
-// ---- banded multi-term mode product (A x, Eq. A_kron) ----------------------------------
+// ---- banded multi-term mode product (A x, Eq. A_kron), T = double or float --------
 constexpr int kMaxBandIn = 4, kMaxBandOut = 4, kMaxBandTerms = 8;
-struct BandTerm {
-  const double *band;  // n x (2p+1) band storage of a 1D matrix
-  int in, out;         // input and output slots
-  double scale;
+template <typename T>
+struct BandTermT {
+  const T *band;  // n x (2p+1) band storage of a 1D matrix
+  int in, out;    // input and output slots
+  T scale;
 };
-struct BandSpec {
-  const double *in[kMaxBandIn];
-  double *out[kMaxBandOut];
+template <typename T>
+struct BandSpecT {
+  const T *in[kMaxBandIn];
+  T *out[kMaxBandOut];
   int n_in, n_out, n_terms, p;
-  BandTerm term[kMaxBandTerms];
+  BandTermT<T> term[kMaxBandTerms];
   // optional: out[last_out](o, n-1, c) += last_add[o * inner + c]  (the W_t term)
-  const double *last_add;
+  const T *last_add;
   int last_out;
 };
-cudaError_t launch_banded_f64(const BandSpec &spec, const ModeView &v, cudaStream_t s);
+using BandTerm = BandTermT<double>;
+using BandSpec = BandSpecT<double>;
+template <typename T>
+cudaError_t launch_banded(const BandSpecT<T> &spec, const ModeView &v, cudaStream_t s);
+inline cudaError_t launch_banded_f64(const BandSpec &spec, const ModeView &v, cudaStream_t s) {
+  return launch_banded<double>(spec, v, s);
+}
 
 // ---- CG vector kernels with deterministic grid reductions --------------------------
 struct CGState {
@@ -57,14 +65,25 @@ int red_grid_for(long long n);
 
 cudaError_t launch_cg_init(const double *F, double *x, double *r, long long N, int B, CGState *st,
                            RedWork rw, cudaStream_t s);
-cudaError_t launch_cg_alpha(const double *p, const double *q, long long N, int B, CGState *st,
-                            RedWork rw, cudaStream_t s);
-cudaError_t launch_cg_xr(double *x, double *r, const double *p, const double *q, long long N, int B,
-                         double tol, CGState *st, RedWork rw, cudaStream_t s);
-cudaError_t launch_cg_beta(const double *z, const double *r, const double *q, long long N, int B,
-                           int flexible, int first, CGState *st, RedWork rw, cudaStream_t s);
-cudaError_t launch_cg_p(const double *z, double *p, long long N, int B, int first, CGState *st,
-                        cudaStream_t s);
+// CG vector kernels for T = double (the solver) or float (inner solves of the
+// refinement form); inner products are accumulated in FP64 either way.
+template <typename T>
+cudaError_t launch_cg_alpha(const T *p, const T *q, long long N, int B, CGState *st, RedWork rw, cudaStream_t s);
+template <typename T>
+cudaError_t launch_cg_xr(T *x, T *r, const T *p, const T *q, long long N, int B, double tol, CGState *st,
+                         RedWork rw, cudaStream_t s);
+template <typename T>
+cudaError_t launch_cg_beta(const T *z, const T *r, const T *q, long long N, int B, int flexible, int first,
+                           CGState *st, RedWork rw, cudaStream_t s);
+template <typename T>
+cudaError_t launch_cg_p(const T *z, T *p, long long N, int B, int first, CGState *st, cudaStream_t s);
+// Refinement form: scaled FP32 inner right-hand side, FP64 correction of u,
+// FP64 residual F - A u with the outer convergence test.
+cudaError_t launch_ir_start(const double *r64, float *r32, float *d, long long N, int B, const CGState *outer,
+                            CGState *inner, RedWork rw, cudaStream_t s);
+cudaError_t launch_ir_correct(double *u, const float *d, long long N, int B, const CGState *outer, cudaStream_t s);
+cudaError_t launch_ir_residual(const double *F, const double *Au, double *r64, long long N, int B, double tol,
+                               CGState *outer, RedWork rw, cudaStream_t s);
 cudaError_t launch_true_residual(const double *F, const double *Ax, long long N, int B, CGState *st,
                                  RedWork rw, cudaStream_t s);
 

@@ -23,6 +23,15 @@ using stls::BandSpec;
 using stls::CGState;
 using stls::ModeView;
 
+// Banded factors and state buffers of the matrix-free A x in one precision.
+template <typename T>
+struct AOps {
+  T *band_M[3] = {}, *band_K[3] = {}, *band_J[3] = {};
+  T *band_Kt = nullptr, *band_Mt = nullptr;
+  T *abuf[8] = {};
+  T *ls_buf = nullptr;
+};
+
 struct stls_ctx {
   stls::HostSetup hs;
   cudaStream_t stream = nullptr;
@@ -30,17 +39,17 @@ struct stls_ctx {
   int n_s[3] = {1, 1, 1};
   long long Ns = 0, N = 0;
   // device factors
-  double *band_M[3] = {}, *band_K[3] = {}, *band_J[3] = {};
-  double *band_Kt = nullptr, *band_Mt = nullptr;
+  AOps<double> a64;                 // FP64 A x (residuals, strict forms)
+  AOps<float> a32;                  // FP32 A x (inner solves of the refinement form)
   double *Uf[4] = {}, *Ub[4] = {};  // U^T (forward) and U (backward), row-major
   double *lam_t = nullptr, *lam_s = nullptr;
   double *e_end = nullptr, *m_int = nullptr;
   // workspace
   double *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr;
   double *fd_tmp[2] = {};
-  double *abuf[8] = {};
-  double *ls_buf = nullptr;
   double *lift_tmp[4] = {};
+  float *ri = nullptr, *pi = nullptr, *qi = nullptr, *zi = nullptr, *di = nullptr;  // refinement inner vectors
+  CGState *st_in = nullptr;
   double *dF = nullptr, *du = nullptr;
   CGState *st = nullptr, *st_host = nullptr;
   stls::RedWork rw{};
@@ -50,8 +59,8 @@ struct stls_ctx {
   std::string err;
   // timing
   bool timing = false;
-  double phase_ms[3] = {0, 0, 0};
-  long long phase_count[3] = {0, 0, 0};
+  double phase_ms[4] = {0, 0, 0, 0};
+  long long phase_count[4] = {0, 0, 0, 0};
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, int>> ev_pairs;  // (phase, first event index)
 };
@@ -158,13 +167,13 @@ ModeView spatial_view(const stls_ctx *c, int k, long long outer_mult) {
 // Dirichlet basis, so int d_kk B_i d_ll B_j = (K_k x K_l x M ...) for k != l.
 // X has `outer_mult` spatial slices.  Outputs (nullable): Ms, Js, Ls over all
 // slices, and Ls_last over the last time slice only (A x needs it for W_t).
-int spatial_tree(stls_ctx *c, const double *X, long long outer_mult, double *Ms, double *Js,
-                 double *Ls, double *Ls_last) {
+template <typename T>
+int spatial_tree(stls_ctx *c, AOps<T> &A, const T *X, long long outer_mult, T *Ms, T *Js, T *Ls, T *Ls_last) {
   const int d = c->d, p = c->hs.prm.p_s;
-  const double *cur[4] = {X, nullptr, nullptr, nullptr};  // m, j, k1, kk
+  const T *cur[4] = {X, nullptr, nullptr, nullptr};  // m, j, k1, kk
   for (int k = 0; k < d - 1; ++k) {
-    double **bank = c->abuf + (k % 2) * 4;
-    BandSpec s{};
+    T **bank = A.abuf + (k % 2) * 4;
+    stls::BandSpecT<T> s{};
     s.p = p;
     int slot_in[4] = {-1, -1, -1, -1};
     for (int a = 0; a < 4; ++a)
@@ -180,23 +189,23 @@ int spatial_tree(stls_ctx *c, const double *X, long long outer_mult, double *Ms,
         slot_out[a] = s.n_out;
         s.out[s.n_out++] = bank[a];
       }
-    auto add = [&](const double *band, int in_state, int out_state, double scale) {
+    auto add = [&](const T *band, int in_state, int out_state, T scale) {
       if (slot_in[in_state] < 0 || slot_out[out_state] < 0) return;
       s.term[s.n_terms++] = {band, slot_in[in_state], slot_out[out_state], scale};
     };
-    add(c->band_M[k], 0, 0, 1.0);
-    add(c->band_M[k], 1, 1, 1.0);
-    add(c->band_J[k], 0, 1, 1.0);
-    add(c->band_M[k], 2, 2, 1.0);
-    add(c->band_K[k], 0, 2, 1.0);
-    add(c->band_M[k], 3, 3, 1.0);
-    add(c->band_K[k], 2, 3, 1.0);
-    STLS_LAUNCH(stls::launch_banded_f64(s, spatial_view(c, k, outer_mult), c->stream), "banded");
+    add(A.band_M[k], 0, 0, T(1));
+    add(A.band_M[k], 1, 1, T(1));
+    add(A.band_J[k], 0, 1, T(1));
+    add(A.band_M[k], 2, 2, T(1));
+    add(A.band_K[k], 0, 2, T(1));
+    add(A.band_M[k], 3, 3, T(1));
+    add(A.band_K[k], 2, 3, T(1));
+    STLS_LAUNCH(stls::launch_banded<T>(s, spatial_view(c, k, outer_mult), c->stream), "banded");
     for (int a = 0; a < 4; ++a) cur[a] = make[a] ? bank[a] : nullptr;
   }
   const int k = d - 1;
   {
-    BandSpec s{};
+    stls::BandSpecT<T> s{};
     s.p = p;
     int slot_in[4] = {-1, -1, -1, -1};
     for (int a = 0; a < 4; ++a)
@@ -208,22 +217,22 @@ int spatial_tree(stls_ctx *c, const double *X, long long outer_mult, double *Ms,
     if (Ms) { o_ms = s.n_out; s.out[s.n_out++] = Ms; }
     if (Js) { o_js = s.n_out; s.out[s.n_out++] = Js; }
     if (Ls) { o_ls = s.n_out; s.out[s.n_out++] = Ls; }
-    auto add = [&](const double *band, int in_state, int out_slot, double scale) {
+    auto add = [&](const T *band, int in_state, int out_slot, T scale) {
       if (slot_in[in_state] < 0 || out_slot < 0) return;
       s.term[s.n_terms++] = {band, slot_in[in_state], out_slot, scale};
     };
-    add(c->band_M[k], 0, o_ms, 1.0);
-    add(c->band_M[k], 1, o_js, 1.0);
-    add(c->band_M[k], 3, o_js, 2.0);
-    add(c->band_J[k], 0, o_js, 1.0);
-    add(c->band_K[k], 2, o_js, 2.0);
-    add(c->band_M[k], 2, o_ls, 1.0);
-    add(c->band_K[k], 0, o_ls, 1.0);
+    add(A.band_M[k], 0, o_ms, T(1));
+    add(A.band_M[k], 1, o_js, T(1));
+    add(A.band_M[k], 3, o_js, T(2));
+    add(A.band_J[k], 0, o_js, T(1));
+    add(A.band_K[k], 2, o_js, T(2));
+    add(A.band_M[k], 2, o_ls, T(1));
+    add(A.band_K[k], 0, o_ls, T(1));
     if (s.n_out > 0)
-      STLS_LAUNCH(stls::launch_banded_f64(s, spatial_view(c, k, outer_mult), c->stream), "banded");
+      STLS_LAUNCH(stls::launch_banded<T>(s, spatial_view(c, k, outer_mult), c->stream), "banded");
     if (Ls_last) {
       // L_s on the last time slice of every right-hand side
-      BandSpec t{};
+      stls::BandSpecT<T> t{};
       t.p = p;
       const long long off = static_cast<long long>(c->n_t - 1) * c->Ns;
       int sm_ = -1, sk1 = -1;
@@ -234,41 +243,42 @@ int spatial_tree(stls_ctx *c, const double *X, long long outer_mult, double *Ms,
         sk1 = t.n_in++;
       }
       t.out[t.n_out++] = Ls_last;
-      t.term[t.n_terms++] = {c->band_K[k], sm_, 0, 1.0};
-      if (sk1 >= 0) t.term[t.n_terms++] = {c->band_M[k], sk1, 0, 1.0};
+      t.term[t.n_terms++] = {A.band_K[k], sm_, 0, T(1)};
+      if (sk1 >= 0) t.term[t.n_terms++] = {A.band_M[k], sk1, 0, T(1)};
       ModeView v = spatial_view(c, k, 1);
       v.outer = c->B;
       v.in_outer_stride = c->N;
       v.out_outer_stride = c->Ns;
-      STLS_LAUNCH(stls::launch_banded_f64(t, v, c->stream), "banded");
+      STLS_LAUNCH(stls::launch_banded<T>(t, v, c->stream), "banded");
     }
   }
   return STLS_OK;
 }
 
-int apply_A_impl(stls_ctx *c, const double *x, double *y) {
+template <typename T>
+int apply_A_impl(stls_ctx *c, AOps<T> &A, const T *x, T *y) {
   const int bank = (c->d - 1) % 2;
-  double *Ms = c->abuf[bank * 4 + 0], *Js = c->abuf[bank * 4 + 1];
-  int rc = spatial_tree(c, x, static_cast<long long>(c->B) * c->n_t, Ms, Js, nullptr, c->ls_buf);
+  T *Ms = A.abuf[bank * 4 + 0], *Js = A.abuf[bank * 4 + 1];
+  int rc = spatial_tree<T>(c, A, x, static_cast<long long>(c->B) * c->n_t, Ms, Js, nullptr, A.ls_buf);
   if (rc) return rc;
-  BandSpec s{};
+  stls::BandSpecT<T> s{};
   s.p = c->hs.prm.p_t;
   s.in[0] = Ms;
   s.in[1] = Js;
   s.n_in = 2;
   s.out[0] = y;
   s.n_out = 1;
-  s.term[0] = {c->band_Kt, 0, 0, 1.0};
-  s.term[1] = {c->band_Mt, 1, 0, 1.0};
+  s.term[0] = {A.band_Kt, 0, 0, T(1)};
+  s.term[1] = {A.band_Mt, 1, 0, T(1)};
   s.n_terms = 2;
-  s.last_add = c->ls_buf;  // W_t x L_s: W_t = e_{n_t} e_{n_t}^T touches the last time slice only
+  s.last_add = A.ls_buf;  // W_t x L_s: W_t = e_{n_t} e_{n_t}^T touches the last time slice only
   s.last_out = 0;
   ModeView v{};
   v.n = c->n_t;
   v.inner = c->Ns;
   v.outer = c->B;
   v.in_outer_stride = v.out_outer_stride = c->N;
-  STLS_LAUNCH(stls::launch_banded_f64(s, v, c->stream), "banded(time)");
+  STLS_LAUNCH(stls::launch_banded<T>(s, v, c->stream), "banded(time)");
   return STLS_OK;
 }
 
@@ -333,7 +343,7 @@ int solve_impl(stls_ctx *c, const double *F, double *u, double tol, int maxit, s
   phase_end(c, ph);
   for (int it = 1; it <= maxit; ++it) {
     ph = phase_begin(c, 0);
-    rc = apply_A_impl(c, c->p, c->q);
+    rc = apply_A_impl<double>(c, c->a64, c->p, c->q);
     if (rc) return rc;
     phase_end(c, ph);
     ph = phase_begin(c, 2);
@@ -358,7 +368,7 @@ int solve_impl(stls_ctx *c, const double *F, double *u, double tol, int maxit, s
     phase_end(c, ph);
   }
   // true FP64 residual ||F - A u|| at exit
-  rc = apply_A_impl(c, u, c->q);
+  rc = apply_A_impl<double>(c, c->a64, u, c->q);
   if (rc) return rc;
   STLS_LAUNCH(stls::launch_true_residual(F, c->q, N, B, c->st, c->rw, c->stream), "true_residual");
   STLS_CK(cudaMemcpyAsync(c->st_host, c->st, sizeof(CGState) * B, cudaMemcpyDeviceToHost, c->stream),
@@ -375,6 +385,7 @@ int solve_impl(stls_ctx *c, const double *F, double *u, double tol, int maxit, s
       info[b].status = status;
       info[b].rel_res = s.rel_res;
       info[b].true_rel_res = s.nF2 > 0 ? std::sqrt(s.true_rr / s.nF2) : 0.0;
+      info[b].outer = 0;
     }
     if (status != STLS_OK && first_bad == STLS_OK) first_bad = status;
   }
@@ -382,6 +393,115 @@ int solve_impl(stls_ctx *c, const double *F, double *u, double tol, int maxit, s
     static const char *names[] = {"ok", "einval", "enomem", "ecuda", "not converged", "breakdown",
                                   "non-finite value"};
     set_err(c, first_bad, std::string("solve: ") + names[first_bad]);
+  }
+  return first_bad;
+}
+
+// Iterative refinement (mixed forms, refine = 1).  Outer loop in FP64:
+// r = F - A u (FP64 A x), stop when ||r|| / ||F|| <= tol; otherwise solve
+// A d = r / ||r|| approximately by flexible CG in FP32 (FP32 vectors and A p,
+// the tensor-core preconditioner, inner products accumulated in FP64) until
+// its residual falls below inner_tol, and update u += ||r|| d in FP64.
+int solve_ir_impl(stls_ctx *c, const double *F, double *u, double tol, int maxit, stls_solve_info *info) {
+  if (!(tol >= 0.0) || maxit < 0) return set_err(c, STLS_EINVAL, "tol must be >= 0 and maxit >= 0");
+  if (check_ptr(c, F, "F") || check_ptr(c, u, "u")) return STLS_EINVAL;
+  const long long N = c->N;
+  const int B = c->B;
+  const double eta = c->hs.prm.inner_tol > 0.0 ? c->hs.prm.inner_tol : 1e-4;
+  const int kMaxOuter = 100;
+  double *r64 = c->r, *q64 = c->q;
+  int ph = phase_begin(c, 2);
+  STLS_LAUNCH(stls::launch_cg_init(F, u, r64, N, B, c->st, c->rw, c->stream), "cg_init");
+  phase_end(c, ph);
+  std::vector<CGState> inner_host(B);
+  int total_inner = 0, outer = 0, rc = STLS_OK;
+  for (; outer < kMaxOuter; ++outer) {
+    STLS_CK(cudaMemcpyAsync(c->st_host, c->st, sizeof(CGState) * B, cudaMemcpyDeviceToHost, c->stream),
+            "state copy");
+    STLS_CK(cudaStreamSynchronize(c->stream), "sync");
+    bool any = false;
+    for (int b = 0; b < B; ++b) any = any || c->st_host[b].active;
+    if (!any || total_inner >= maxit) break;
+    // ---- inner flexible CG in FP32 on A d = r / ||r|| ----
+    ph = phase_begin(c, 2);
+    STLS_LAUNCH(stls::launch_ir_start(r64, c->ri, c->di, N, B, c->st, c->st_in, c->rw, c->stream), "ir_start");
+    phase_end(c, ph);
+    ph = phase_begin(c, 1);
+    c->launches += stls::tc_fd_launch_count(c->tc);
+    STLS_CK(stls::tc_fd_apply_f32(c->tc, c->ri, c->zi, c->stream), "tensor-core FD apply");
+    phase_end(c, ph);
+    ph = phase_begin(c, 2);
+    STLS_LAUNCH(stls::launch_cg_beta<float>(c->zi, c->ri, c->qi, N, B, 1, 1, c->st_in, c->rw, c->stream),
+                "cg_beta");
+    STLS_LAUNCH(stls::launch_cg_p<float>(c->zi, c->pi, N, B, 1, c->st_in, c->stream), "cg_p");
+    phase_end(c, ph);
+    const int budget = maxit - total_inner;
+    for (int it = 1; it <= budget; ++it) {
+      ph = phase_begin(c, 3);
+      rc = apply_A_impl<float>(c, c->a32, c->pi, c->qi);
+      if (rc) return rc;
+      phase_end(c, ph);
+      ph = phase_begin(c, 2);
+      STLS_LAUNCH(stls::launch_cg_alpha<float>(c->pi, c->qi, N, B, c->st_in, c->rw, c->stream), "cg_alpha");
+      STLS_LAUNCH(stls::launch_cg_xr<float>(c->di, c->ri, c->pi, c->qi, N, B, eta, c->st_in, c->rw, c->stream),
+                  "cg_xr");
+      phase_end(c, ph);
+      STLS_CK(cudaMemcpyAsync(inner_host.data(), c->st_in, sizeof(CGState) * B, cudaMemcpyDeviceToHost,
+                              c->stream),
+              "state copy");
+      STLS_CK(cudaStreamSynchronize(c->stream), "sync");
+      if (stls::tc_fd_error(c->tc))
+        return set_err(c, STLS_ECUDA, "tensor-core FD apply: a bounded mbarrier wait timed out");
+      bool inner_any = false;
+      for (int b = 0; b < B; ++b) inner_any = inner_any || inner_host[b].active;
+      if (!inner_any) break;
+      ph = phase_begin(c, 1);
+      c->launches += stls::tc_fd_launch_count(c->tc);
+      STLS_CK(stls::tc_fd_apply_f32(c->tc, c->ri, c->zi, c->stream), "tensor-core FD apply");
+      phase_end(c, ph);
+      ph = phase_begin(c, 2);
+      STLS_LAUNCH(stls::launch_cg_beta<float>(c->zi, c->ri, c->qi, N, B, 1, 0, c->st_in, c->rw, c->stream),
+                  "cg_beta");
+      STLS_LAUNCH(stls::launch_cg_p<float>(c->zi, c->pi, N, B, 0, c->st_in, c->stream), "cg_p");
+      phase_end(c, ph);
+    }
+    int its = 0;
+    for (int b = 0; b < B; ++b) its = std::max(its, inner_host[b].iters);
+    total_inner += std::max(its, 1);
+    // ---- FP64 correction and residual ----
+    ph = phase_begin(c, 2);
+    STLS_LAUNCH(stls::launch_ir_correct(u, c->di, N, B, c->st, c->stream), "ir_correct");
+    phase_end(c, ph);
+    ph = phase_begin(c, 0);
+    rc = apply_A_impl<double>(c, c->a64, u, q64);
+    if (rc) return rc;
+    phase_end(c, ph);
+    ph = phase_begin(c, 2);
+    STLS_LAUNCH(stls::launch_ir_residual(F, q64, r64, N, B, tol, c->st, c->rw, c->stream), "ir_residual");
+    phase_end(c, ph);
+  }
+  STLS_CK(cudaMemcpyAsync(c->st_host, c->st, sizeof(CGState) * B, cudaMemcpyDeviceToHost, c->stream),
+          "state copy");
+  STLS_CK(cudaStreamSynchronize(c->stream), "sync");
+  if (c->timing) collect_phases(c);
+  int first_bad = STLS_OK;
+  for (int b = 0; b < B; ++b) {
+    const CGState &s = c->st_host[b];
+    int status = s.status;
+    if (status == STLS_OK && s.active) status = STLS_ENOTCONV;
+    if (info != nullptr) {
+      info[b].iters = total_inner;
+      info[b].status = status;
+      info[b].rel_res = s.rel_res;
+      info[b].true_rel_res = s.nF2 > 0 ? std::sqrt(s.rr / s.nF2) : 0.0;
+      info[b].outer = s.iters;
+    }
+    if (status != STLS_OK && first_bad == STLS_OK) first_bad = status;
+  }
+  if (first_bad != STLS_OK) {
+    static const char *names[] = {"ok", "einval", "enomem", "ecuda", "not converged", "breakdown",
+                                  "non-finite value"};
+    set_err(c, first_bad, std::string("solve (refinement): ") + names[first_bad]);
   }
   return first_bad;
 }
@@ -441,17 +561,29 @@ int stls_create(stls_ctx **out, const stls_params *prm, void *cuda_stream) {
     return code;
   };
   int rc = STLS_OK;
+  const bool refine = P.refine != 0;
+  auto to_f32 = [](const std::vector<double> &v) { return std::vector<float>(v.begin(), v.end()); };
   for (int k = 0; k < c->d && !rc; ++k) {
     const stls::Dir1D &D = c->hs.space[k];
-    rc = upload(c, &c->band_M[k], stls::to_band(D.M, D.n, D.p));
-    if (!rc) rc = upload(c, &c->band_K[k], stls::to_band(D.K, D.n, D.p));
-    if (!rc) rc = upload(c, &c->band_J[k], stls::to_band(D.J, D.n, D.p));
+    const std::vector<double> bM = stls::to_band(D.M, D.n, D.p), bK = stls::to_band(D.K, D.n, D.p),
+                              bJ = stls::to_band(D.J, D.n, D.p);
+    rc = upload(c, &c->a64.band_M[k], bM);
+    if (!rc) rc = upload(c, &c->a64.band_K[k], bK);
+    if (!rc) rc = upload(c, &c->a64.band_J[k], bJ);
+    if (!rc && refine) rc = upload(c, &c->a32.band_M[k], to_f32(bM));
+    if (!rc && refine) rc = upload(c, &c->a32.band_K[k], to_f32(bK));
+    if (!rc && refine) rc = upload(c, &c->a32.band_J[k], to_f32(bJ));
     if (!rc) rc = upload(c, &c->Uf[k], transpose(c->hs.eig_s[k].U, D.n));
     if (!rc) rc = upload(c, &c->Ub[k], c->hs.eig_s[k].U);
   }
   const stls::Dir1D &Tm = c->hs.time;
-  if (!rc) rc = upload(c, &c->band_Kt, stls::to_band(Tm.K, Tm.n, Tm.p));
-  if (!rc) rc = upload(c, &c->band_Mt, stls::to_band(Tm.M, Tm.n, Tm.p));
+  {
+    const std::vector<double> bKt = stls::to_band(Tm.K, Tm.n, Tm.p), bMt = stls::to_band(Tm.M, Tm.n, Tm.p);
+    if (!rc) rc = upload(c, &c->a64.band_Kt, bKt);
+    if (!rc) rc = upload(c, &c->a64.band_Mt, bMt);
+    if (!rc && refine) rc = upload(c, &c->a32.band_Kt, to_f32(bKt));
+    if (!rc && refine) rc = upload(c, &c->a32.band_Mt, to_f32(bMt));
+  }
   if (!rc) rc = upload(c, &c->Uf[c->d], transpose(c->hs.eig_t.U, Tm.n));
   if (!rc) rc = upload(c, &c->Ub[c->d], c->hs.eig_t.U);
   if (!rc) rc = upload(c, &c->lam_t, c->hs.eig_t.lam);
@@ -476,8 +608,16 @@ int stls_create(stls_ctx **out, const stls_params *prm, void *cuda_stream) {
   double **vecs[] = {&c->r, &c->p, &c->q, &c->z, &c->fd_tmp[0], &c->fd_tmp[1], &c->dF, &c->du};
   for (double **v : vecs)
     if (!rc) rc = dev_alloc(c, v, BN);
-  for (int a = 0; a < 8 && !rc; ++a) rc = dev_alloc(c, &c->abuf[a], BN);
-  if (!rc) rc = dev_alloc(c, &c->ls_buf, BNs);
+  for (int a = 0; a < 8 && !rc; ++a) rc = dev_alloc(c, &c->a64.abuf[a], BN);
+  if (!rc) rc = dev_alloc(c, &c->a64.ls_buf, BNs);
+  if (refine) {
+    for (int a = 0; a < 8 && !rc; ++a) rc = dev_alloc(c, &c->a32.abuf[a], BN);
+    if (!rc) rc = dev_alloc(c, &c->a32.ls_buf, BNs);
+    float **iv[] = {&c->ri, &c->pi, &c->qi, &c->zi, &c->di};
+    for (float **v : iv)
+      if (!rc) rc = dev_alloc(c, v, BN);
+    if (!rc) rc = dev_alloc(c, &c->st_in, c->B);
+  }
   for (int a = 0; a < 4 && !rc; ++a) rc = dev_alloc(c, &c->lift_tmp[a], BNs);
   if (!rc) rc = dev_alloc(c, &c->st, c->B);
   c->rw.grid = stls::red_grid_for(c->N);
@@ -490,7 +630,8 @@ int stls_create(stls_ctx **out, const stls_params *prm, void *cuda_stream) {
     return fail(STLS_ENOMEM);
   }
   if (cudaMemset(c->rw.tickets, 0, sizeof(unsigned) * c->B) != cudaSuccess ||
-      cudaMemset(c->st, 0, sizeof(CGState) * c->B) != cudaSuccess) {
+      cudaMemset(c->st, 0, sizeof(CGState) * c->B) != cudaSuccess ||
+      (c->st_in != nullptr && cudaMemset(c->st_in, 0, sizeof(CGState) * c->B) != cudaSuccess)) {
     c->err = "cudaMemset failed";
     return fail(STLS_ECUDA);
   }
@@ -539,7 +680,7 @@ int stls_apply_A(stls_ctx *c, const double *x, double *y) {
   if (c == nullptr) return STLS_EINVAL;
   if (check_ptr(c, x, "x") || check_ptr(c, y, "y")) return STLS_EINVAL;
   if (x == y) return set_err(c, STLS_EINVAL, "apply_A: x and y must not overlap");
-  return apply_A_impl(c, x, y);
+  return apply_A_impl<double>(c, c->a64, x, y);
 }
 
 int stls_apply_precond(stls_ctx *c, const double *r, double *z) {
@@ -551,7 +692,7 @@ int stls_apply_precond(stls_ctx *c, const double *r, double *z) {
 int stls_solve(stls_ctx *c, const double *F, double *u, double tol, int maxit, stls_solve_info *info) {
   if (c == nullptr) return STLS_EINVAL;
   if (F == u) return set_err(c, STLS_EINVAL, "solve: F and u must not overlap");
-  return solve_impl(c, F, u, tol, maxit, info);
+  return c->hs.prm.refine ? solve_ir_impl(c, F, u, tol, maxit, info) : solve_impl(c, F, u, tol, maxit, info);
 }
 
 int stls_solve_host(stls_ctx *c, const double *F_host, double *u_host, double tol, int maxit,
@@ -559,7 +700,8 @@ int stls_solve_host(stls_ctx *c, const double *F_host, double *u_host, double to
   if (c == nullptr || F_host == nullptr || u_host == nullptr) return set_err(c, STLS_EINVAL, "NULL argument");
   const size_t bytes = sizeof(double) * static_cast<size_t>(c->B) * c->N;
   STLS_CK(cudaMemcpyAsync(c->dF, F_host, bytes, cudaMemcpyHostToDevice, c->stream), "H2D copy of F");
-  int rc = solve_impl(c, c->dF, c->du, tol, maxit, info);
+  int rc = c->hs.prm.refine ? solve_ir_impl(c, c->dF, c->du, tol, maxit, info)
+                            : solve_impl(c, c->dF, c->du, tol, maxit, info);
   if (rc != STLS_OK && rc != STLS_ENOTCONV && rc != STLS_EBREAKDOWN && rc != STLS_ENONFINITE) return rc;
   STLS_CK(cudaMemcpyAsync(u_host, c->du, bytes, cudaMemcpyDeviceToHost, c->stream), "D2H copy of u");
   STLS_CK(cudaStreamSynchronize(c->stream), "sync");
@@ -570,7 +712,7 @@ int stls_apply_lift(stls_ctx *c, const double *c0, double *y) {
   if (c == nullptr) return STLS_EINVAL;
   if (check_ptr(c, c0, "c0") || check_ptr(c, y, "y")) return STLS_EINVAL;
   double *Js = c->lift_tmp[0], *Ls = c->lift_tmp[1];
-  int rc = spatial_tree(c, c0, c->B, nullptr, Js, Ls, nullptr);
+  int rc = spatial_tree<double>(c, c->a64, c0, c->B, nullptr, Js, Ls, nullptr);
   if (rc) return rc;
   STLS_LAUNCH(stls::launch_lift_combine(Ls, Js, c->e_end, c->m_int, y, c->Ns, c->n_t, c->B, c->stream),
               "lift_combine");
@@ -585,11 +727,11 @@ int stls_lift_adjoint(stls_ctx *c, const double *g, const double *lam, double *d
   STLS_LAUNCH(stls::launch_lift_reduce(lam, g, c->e_end, c->m_int, a, bs, gs, c->Ns, c->n_t, c->B,
                                        c->stream),
               "lift_reduce");
-  double *La = c->ls_buf;           // B x N_s
+  double *La = c->a64.ls_buf;       // B x N_s
   double *Jb = c->lift_tmp[3];
-  int rc = spatial_tree(c, a, c->B, nullptr, nullptr, La, nullptr);
+  int rc = spatial_tree<double>(c, c->a64, a, c->B, nullptr, nullptr, La, nullptr);
   if (rc) return rc;
-  rc = spatial_tree(c, bs, c->B, nullptr, Jb, nullptr, nullptr);
+  rc = spatial_tree<double>(c, c->a64, bs, c->B, nullptr, Jb, nullptr, nullptr);
   if (rc) return rc;
   const long long n = static_cast<long long>(c->B) * c->Ns;
   STLS_LAUNCH(stls::launch_axpy(gs, La, -1.0, dc0, n, c->stream), "axpy");
@@ -607,7 +749,7 @@ long long stls_launch_count(const stls_ctx *c) { return c == nullptr ? 0 : c->la
 int stls_enable_timing(stls_ctx *c, int on) {
   if (c == nullptr) return STLS_EINVAL;
   c->timing = on != 0;
-  for (int i = 0; i < 3; ++i) {
+  for (int i = 0; i < 4; ++i) {
     c->phase_ms[i] = 0.0;
     c->phase_count[i] = 0;
   }
@@ -615,11 +757,11 @@ int stls_enable_timing(stls_ctx *c, int on) {
   return STLS_OK;
 }
 
-int stls_phase_times(stls_ctx *c, double *ms_out3, long long *count_out3) {
+int stls_phase_times(stls_ctx *c, double *ms_out4, long long *count_out4) {
   if (c == nullptr) return STLS_EINVAL;
-  for (int i = 0; i < 3; ++i) {
-    if (ms_out3) ms_out3[i] = c->phase_ms[i];
-    if (count_out3) count_out3[i] = c->phase_count[i];
+  for (int i = 0; i < 4; ++i) {
+    if (ms_out4) ms_out4[i] = c->phase_ms[i];
+    if (count_out4) count_out4[i] = c->phase_count[i];
   }
   return STLS_OK;
 }

@@ -474,7 +474,12 @@ cudaError_t tc_fd_create(TcFd &tc, int precision, int d, const int *n, int B,
   return cudaSuccess;
 }
 
-cudaError_t tc_fd_apply(TcFd &tc, const double *r, double *z, cudaStream_t s) {
+namespace {
+
+// The 2(d+1) passes; IO is the type of r and z (double, or float for the inner
+// solves of the refinement form).
+template <typename IO>
+cudaError_t apply_passes(TcFd &tc, const IO *r, IO *z, cudaStream_t s) {
   Impl *im = static_cast<Impl *>(tc.impl);
   if (im == nullptr) return cudaErrorNotReady;
   const int d = tc.d, nprod = 2 * (d + 1);
@@ -504,18 +509,18 @@ cudaError_t tc_fd_apply(TcFd &tc, const double *r, double *z, cudaStream_t s) {
     cudaError_t e;
     if (kind == KIND_BF16) {
       if (st == 0)
-        e = launch_pass<double, __nv_bfloat16, KIND_BF16, false>(p, im->sms, s);
+        e = launch_pass<IO, __nv_bfloat16, KIND_BF16, false>(p, im->sms, s);
       else if (st == nprod - 1)
-        e = launch_pass<__nv_bfloat16, double, KIND_BF16, false>(p, im->sms, s);
+        e = launch_pass<__nv_bfloat16, IO, KIND_BF16, false>(p, im->sms, s);
       else if (divide)
         e = launch_pass<__nv_bfloat16, __nv_bfloat16, KIND_BF16, true>(p, im->sms, s);
       else
         e = launch_pass<__nv_bfloat16, __nv_bfloat16, KIND_BF16, false>(p, im->sms, s);
     } else {
       if (st == 0)
-        e = launch_pass<double, float, KIND_TF32, false>(p, im->sms, s);
+        e = launch_pass<IO, float, KIND_TF32, false>(p, im->sms, s);
       else if (st == nprod - 1)
-        e = launch_pass<float, double, KIND_TF32, false>(p, im->sms, s);
+        e = launch_pass<float, IO, KIND_TF32, false>(p, im->sms, s);
       else if (divide)
         e = launch_pass<float, float, KIND_TF32, true>(p, im->sms, s);
       else
@@ -525,6 +530,12 @@ cudaError_t tc_fd_apply(TcFd &tc, const double *r, double *z, cudaStream_t s) {
   }
   return cudaSuccess;
 }
+
+}  // namespace
+
+cudaError_t tc_fd_apply(TcFd &tc, const double *r, double *z, cudaStream_t s) { return apply_passes<double>(tc, r, z, s); }
+
+cudaError_t tc_fd_apply_f32(TcFd &tc, const float *r, float *z, cudaStream_t s) { return apply_passes<float>(tc, r, z, s); }
 
 int tc_fd_error(const TcFd &tc) {
   const Impl *im = static_cast<const Impl *>(tc.impl);

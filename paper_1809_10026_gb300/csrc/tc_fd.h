@@ -27,6 +27,8 @@ cudaError_t tc_fd_create(TcFd &tc, int precision, int d, const int *n, int B,
                          const std::vector<std::vector<double>> &U, const double *lam_t_dev,
                          const double *lam_s_dev, std::string &err);
 cudaError_t tc_fd_apply(TcFd &tc, const double *r, double *z, cudaStream_t s);
+// Same with FP32 r and z (inner solves of the refinement form).
+cudaError_t tc_fd_apply_f32(TcFd &tc, const float *r, float *z, cudaStream_t s);
 int tc_fd_launch_count(const TcFd &tc);
 // Non-zero once a tensor-core kernel gave up on a bounded wait (host-mapped
 // flag; read it after synchronizing the stream).

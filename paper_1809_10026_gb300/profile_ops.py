@@ -26,8 +26,9 @@ def main():
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=2)
     ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--refine", action="store_true", help="iterative-refinement form (mixed precisions)")
     a = ap.parse_args()
-    S = stls.Solver(a.d, a.p, a.n_el, precision=a.precision, batch=a.batch)
+    S = stls.Solver(a.d, a.p, a.n_el, precision=a.precision, batch=a.batch, refine=a.refine)
     x = torch.from_numpy(synth.uniform(S.N, 4, batch=a.batch)).cuda()
     y = torch.empty_like(x)
 
@@ -39,8 +40,18 @@ def main():
         else:
             S.solve(x, a.tol, 500, out=y)
 
+    info = None
+
+    def run_solve():
+        nonlocal info
+        _, info = S.solve(x, a.tol, 1000, out=y)
+
+    if a.op == "solve":
+        run = run_solve  # noqa: F811
     for _ in range(a.warmup):
         run()
+    if a.op == "solve":
+        S.enable_timing(True)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     l0 = S.launch_count()
@@ -50,8 +61,12 @@ def main():
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / a.reps
-    print(json.dumps({"op": a.op, "precision": a.precision, "N": S.N, "batch": a.batch, "ms": ms,
-                      "launches_per_rep": (S.launch_count() - l0) / a.reps}))
+    out = {"op": a.op, "precision": a.precision, "refine": a.refine, "N": S.N, "batch": a.batch, "ms": ms,
+           "launches_per_rep": (S.launch_count() - l0) / a.reps}
+    if info is not None:
+        out["info"] = info[0]
+        out["phases_ms_per_rep"] = {k: (v[0] / a.reps, v[1] / a.reps) for k, v in S.phase_times().items()}
+    print(json.dumps(out))
 
 
 if __name__ == "__main__":

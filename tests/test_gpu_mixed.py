@@ -90,3 +90,37 @@ def test_mixed_solve_cfg4_bf16():
     u, info = S.solve(F, tol=1e-8, maxit=200)
     assert info[0]["status"] == "ok" and info[0]["true_rel_res"] <= 1.5e-8
     assert info[0]["iters"] <= 40
+
+
+@pytest.mark.parametrize("form", ["bf16", "tf32"])
+def test_refinement_solve_cfg3(form):
+    """Iterative refinement: FP64 residual F - A u, inner FP32 flexible CG with the
+    tensor-core preconditioner; the stopping test is on the true FP64 residual."""
+    pi = np.pi
+    prob = STProblem(3, 4, 32)
+    s = lambda x: np.sin(pi * x)
+    F = prob.load_separable([(1.0, np.cos, [s, s, s]), (3 * pi ** 2, np.sin, [s, s, s])])
+    Fg = torch.from_numpy(F).cuda()
+    u64, _ = _solver(3, 4, 32).solve(Fg, tol=1e-12, maxit=300)
+    S = _solver(3, 4, 32, precision=form, refine=True)
+    u8, i8 = S.solve(Fg, tol=1e-8, maxit=400)
+    assert i8[0]["status"] == "ok" and i8[0]["true_rel_res"] <= 1e-8 and i8[0]["outer"] >= 2
+    u12, i12 = S.solve(Fg, tol=1e-12, maxit=800)
+    assert i12[0]["status"] == "ok" and i12[0]["true_rel_res"] <= 1e-12
+    assert _rel(u12.cpu().numpy(), u64.cpu().numpy()) <= 1e-8
+    print(form, "refine: inner", i8[0]["iters"], "outer", i8[0]["outer"], "| 1e-12:", i12[0]["iters"], i12[0]["outer"])
+
+
+def test_refinement_batch_matches_direct_solve():
+    from oracle.solve import direct_solve
+    prob = STProblem(2, 3, 7)
+    A = prob.assemble_A_kron()
+    F = synth.uniform(prob.N, 77, batch=3)
+    F[1] *= 1e-4
+    S = _solver(2, 3, 7, precision="bf16", refine=True, batch=3)
+    u, info = S.solve(torch.from_numpy(F).cuda(), tol=1e-12, maxit=500)
+    u = u.cpu().numpy()
+    for b in range(3):
+        ref = direct_solve(A, F[b])
+        assert info[b]["status"] == "ok"
+        assert np.linalg.norm(u[b] - ref) / np.linalg.norm(ref) <= 1e-10
