@@ -22,6 +22,26 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// Inner products of FP32 vectors: compensated FP32 accumulation (TwoProd by
+// FMA and TwoSum; the "Dot2" scheme of Ogita, Rump and Oishi, 2005), whose
+// error is about eps_32 |x.y| + (n eps_32)^2 sum|x_i y_i| for the n terms of one
+// thread, converted to FP64 once per thread.  On this part FP64 instructions
+// issue at a small fraction of the FP32 rate, so converting and accumulating
+// every term in FP64 would bound these kernels by the FP64 pipe.
+struct Dot2f {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float a, float b) {
+    const float h = __fmul_rn(a, b);
+    const float l = __fmaf_rn(a, b, -h);  // a b = h + l exactly
+    const float t = __fadd_rn(s, h);
+    const float z = __fsub_rn(t, s);
+    const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(h, z));  // s + h = t + e exactly
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(l, e));
+  }
+  __device__ __forceinline__ double value() const { return static_cast<double>(s) + static_cast<double>(c); }
+};
+
 // Block-wide sums of NV values, result valid in thread 0.
 template <int NV>
 __device__ void block_sum(double (&v)[NV]) {
@@ -116,9 +136,17 @@ __global__ void __launch_bounds__(kThreads)
   const int b = blockIdx.y;
   const T *pb = p + static_cast<size_t>(b) * N, *qb = q + static_cast<size_t>(b) * N;
   double v[1] = {0.0};
-  for (long long i = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x; i < N;
-       i += static_cast<long long>(gridDim.x) * kThreads)
-    v[0] = fma(static_cast<double>(pb[i]), static_cast<double>(qb[i]), v[0]);
+  if constexpr (sizeof(T) == 4) {
+    Dot2f acc;
+    for (long long i = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x; i < N;
+         i += static_cast<long long>(gridDim.x) * kThreads)
+      acc.add(pb[i], qb[i]);
+    v[0] = acc.value();
+  } else {
+    for (long long i = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x; i < N;
+         i += static_cast<long long>(gridDim.x) * kThreads)
+      v[0] = fma(static_cast<double>(pb[i]), static_cast<double>(qb[i]), v[0]);
+  }
   double tot[1];
   if (grid_sum<1>(v, rw, b, tot) && threadIdx.x == 0) {
     CGState &s = st[b];
@@ -147,12 +175,24 @@ __global__ void __launch_bounds__(kThreads)
   const T *pb = p + static_cast<size_t>(b) * N, *qb = q + static_cast<size_t>(b) * N;
   double v[1] = {0.0};
   if (active) {
-    for (long long i = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x; i < N;
-         i += static_cast<long long>(gridDim.x) * kThreads) {
-      xb[i] = fma(alpha, pb[i], xb[i]);
-      T ri = fma(-alpha, qb[i], rb[i]);
-      rb[i] = ri;
-      v[0] = fma(static_cast<double>(ri), static_cast<double>(ri), v[0]);
+    if constexpr (sizeof(T) == 4) {
+      Dot2f acc;
+      for (long long i = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x; i < N;
+           i += static_cast<long long>(gridDim.x) * kThreads) {
+        xb[i] = fma(alpha, pb[i], xb[i]);
+        const T ri = fma(-alpha, qb[i], rb[i]);
+        rb[i] = ri;
+        acc.add(ri, ri);
+      }
+      v[0] = acc.value();
+    } else {
+      for (long long i = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x; i < N;
+           i += static_cast<long long>(gridDim.x) * kThreads) {
+        xb[i] = fma(alpha, pb[i], xb[i]);
+        const T ri = fma(-alpha, qb[i], rb[i]);
+        rb[i] = ri;
+        v[0] = fma(static_cast<double>(ri), static_cast<double>(ri), v[0]);
+      }
     }
   }
   double tot[1];
@@ -181,11 +221,23 @@ __global__ void __launch_bounds__(kThreads)
   const T *qb = q + static_cast<size_t>(b) * N;
   const bool need_zq = flexible && !first;
   double v[2] = {0.0, 0.0};
-  for (long long i = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x; i < N;
-       i += static_cast<long long>(gridDim.x) * kThreads) {
-    const double zi = static_cast<double>(zb[i]);
-    v[0] = fma(zi, static_cast<double>(rb[i]), v[0]);
-    if (need_zq) v[1] = fma(zi, static_cast<double>(qb[i]), v[1]);
+  if constexpr (sizeof(T) == 4) {
+    Dot2f zr, zq;
+    for (long long i = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x; i < N;
+         i += static_cast<long long>(gridDim.x) * kThreads) {
+      const T zi = zb[i];
+      zr.add(zi, rb[i]);
+      if (need_zq) zq.add(zi, qb[i]);
+    }
+    v[0] = zr.value();
+    v[1] = zq.value();
+  } else {
+    for (long long i = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x; i < N;
+         i += static_cast<long long>(gridDim.x) * kThreads) {
+      const double zi = static_cast<double>(zb[i]);
+      v[0] = fma(zi, static_cast<double>(rb[i]), v[0]);
+      if (need_zq) v[1] = fma(zi, static_cast<double>(qb[i]), v[1]);
+    }
   }
   double tot[2];
   if (grid_sum<2>(v, rw, b, tot) && threadIdx.x == 0) {
@@ -367,7 +419,7 @@ unsigned grid_1d(long long n) {
 
 int red_grid_for(long long n) {
   long long g = (n + kThreads * 8 - 1) / (kThreads * 8);
-  if (g > 1024) g = 1024;
+  if (g > 1216) g = 1216;  // 8 blocks of 256 threads on each of the 152 SMs
   return static_cast<int>(g < 1 ? 1 : g);
 }
 

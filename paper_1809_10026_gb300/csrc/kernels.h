@@ -19,6 +19,50 @@ struct ModeView {
   long long out_outer_stride;
 };
 
+// ---- fused A x for two and three spatial directions (k_apply_a.cu) -------------------
+// Band rows are padded to band_row_stride(p, sizeof(T)) elements (whole 16-byte
+// vectors); b2K holds 2 K exactly.
+constexpr int kFusedMaxP = 5;
+int band_row_stride(int p, int elem_bytes);
+bool fused_A_supported(int d, int p_s, int p_t);
+
+template <typename T>
+struct SliceArgs {
+  const T *x;
+  T *out_m, *out_j, *out_k;  // states after directions 1, 2 (out_k unused when ls_last is set)
+  T *ls_last;                // two spatial directions: L_s x of the last time slice, per b
+  const T *bM1, *bJ1, *bK1, *bM2, *bJ2, *bK2, *b2K2;
+  long long slices;  // number of n2 x n1 slices
+  int n1, n2, n_t, row_stride;
+};
+template <typename T>
+struct ZArgs {
+  const T *m, *j, *k;
+  T *Ms, *Js, *ls_last;
+  const T *bM, *bJ, *bK, *b2K;
+  long long outer, inner;  // outer = B n_t, inner = n1 n2
+  int n, n_t, row_stride;
+};
+template <typename T>
+struct TArgs {
+  const T *Ms, *Js, *ls_last;
+  T *y;
+  const T *bK, *bM;
+  long long outer, inner;  // outer = B, inner = N_s
+  int n, row_stride;
+};
+template <typename T>
+struct FusedA {
+  int d, p_s, p_t, n[3], n_t, B;
+  const T *bM[3], *bJ[3], *bK[3], *b2K[3];  // padded spatial bands
+  const T *bKt, *bMt;                       // padded time bands
+  T *work[5];                               // d = 3: m, j', k, M_s x, J_s x; d = 2: work[3..4]
+  T *ls_last;                               // B * N_s
+};
+// y = A x; 2 launches (d = 2) or 3 (d = 3).  x, y: B * N values, colexicographic.
+template <typename T>
+cudaError_t launch_fused_A(const FusedA<T> &f, const T *x, T *y, cudaStream_t s);
+
 // ---- dense mode product: out = in x_k W (Algorithm 1, steps 2 and 4) -----------------
 // out(o, i, c) = sum_j W[i * n + j] in(o, j, c).  If lam_row != nullptr the
 // result is divided by lam_row[i] + lam_col[c] (Algorithm 1, step 3).
@@ -47,6 +91,7 @@ using BandTerm = BandTermT<double>;
 using BandSpec = BandSpecT<double>;
 template <typename T>
 cudaError_t launch_banded(const BandSpecT<T> &spec, const ModeView &v, cudaStream_t s);
+
 inline cudaError_t launch_banded_f64(const BandSpec &spec, const ModeView &v, cudaStream_t s) {
   return launch_banded<double>(spec, v, s);
 }
@@ -66,7 +111,8 @@ int red_grid_for(long long n);
 cudaError_t launch_cg_init(const double *F, double *x, double *r, long long N, int B, CGState *st,
                            RedWork rw, cudaStream_t s);
 // CG vector kernels for T = double (the solver) or float (inner solves of the
-// refinement form); inner products are accumulated in FP64 either way.
+// refinement form); FP64 inner products accumulate in FP64, FP32 ones in
+// compensated FP32 (twice-working-precision accuracy) per thread and FP64 across.
 template <typename T>
 cudaError_t launch_cg_alpha(const T *p, const T *q, long long N, int B, CGState *st, RedWork rw, cudaStream_t s);
 template <typename T>

@@ -28,6 +28,9 @@ template <typename T>
 struct AOps {
   T *band_M[3] = {}, *band_K[3] = {}, *band_J[3] = {};
   T *band_Kt = nullptr, *band_Mt = nullptr;
+  // the same bands with rows padded to whole 16-byte vectors, and 2 K (fused A x)
+  T *pad_M[3] = {}, *pad_K[3] = {}, *pad_J[3] = {}, *pad_2K[3] = {};
+  T *pad_Kt = nullptr, *pad_Mt = nullptr;
   T *abuf[8] = {};
   T *ls_buf = nullptr;
 };
@@ -107,6 +110,27 @@ int upload(stls_ctx *c, T **ptr, const std::vector<T> &h) {
   if (rc) return rc;
   STLS_CK(cudaMemcpy(*ptr, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice), "upload");
   return STLS_OK;
+}
+
+// Band rows (2p+1 values) copied into rows of `stride` values, scaled by `scale`.
+template <typename T>
+std::vector<T> pad_band(const std::vector<double> &band, int n, int p, int stride, double scale) {
+  const int w = 2 * p + 1;
+  std::vector<T> out(static_cast<size_t>(n) * stride, T(0));
+  for (int i = 0; i < n; ++i)
+    for (int o = 0; o < w; ++o) out[static_cast<size_t>(i) * stride + o] = static_cast<T>(scale * band[i * w + o]);
+  return out;
+}
+
+template <typename T>
+int upload_padded(stls_ctx *c, AOps<T> &A, int k, const stls::Dir1D &D, const std::vector<double> &bM,
+                  const std::vector<double> &bK, const std::vector<double> &bJ) {
+  const int st = stls::band_row_stride(D.p, sizeof(T));
+  int rc = upload(c, &A.pad_M[k], pad_band<T>(bM, D.n, D.p, st, 1.0));
+  if (!rc) rc = upload(c, &A.pad_K[k], pad_band<T>(bK, D.n, D.p, st, 1.0));
+  if (!rc) rc = upload(c, &A.pad_J[k], pad_band<T>(bJ, D.n, D.p, st, 1.0));
+  if (!rc) rc = upload(c, &A.pad_2K[k], pad_band<T>(bK, D.n, D.p, st, 2.0));
+  return rc;
 }
 
 std::vector<double> transpose(const std::vector<double> &A, int n) {
@@ -257,6 +281,28 @@ int spatial_tree(stls_ctx *c, AOps<T> &A, const T *X, long long outer_mult, T *M
 
 template <typename T>
 int apply_A_impl(stls_ctx *c, AOps<T> &A, const T *x, T *y) {
+  if (stls::fused_A_supported(c->d, c->hs.prm.p_s, c->hs.prm.p_t)) {
+    stls::FusedA<T> f{};
+    f.d = c->d;
+    f.p_s = c->hs.prm.p_s;
+    f.p_t = c->hs.prm.p_t;
+    for (int k = 0; k < c->d; ++k) {
+      f.n[k] = c->n_s[k];
+      f.bM[k] = A.pad_M[k];
+      f.bJ[k] = A.pad_J[k];
+      f.bK[k] = A.pad_K[k];
+      f.b2K[k] = A.pad_2K[k];
+    }
+    f.n_t = c->n_t;
+    f.B = c->B;
+    f.bKt = A.pad_Kt;
+    f.bMt = A.pad_Mt;
+    for (int w = 0; w < 5; ++w) f.work[w] = A.abuf[w];
+    f.ls_last = A.ls_buf;
+    c->launches += c->d - 1;  // d launches in all
+    STLS_LAUNCH(stls::launch_fused_A<T>(f, x, y, c->stream), "fused A x");
+    return STLS_OK;
+  }
   const int bank = (c->d - 1) % 2;
   T *Ms = A.abuf[bank * 4 + 0], *Js = A.abuf[bank * 4 + 1];
   int rc = spatial_tree<T>(c, A, x, static_cast<long long>(c->B) * c->n_t, Ms, Js, nullptr, A.ls_buf);
@@ -573,6 +619,8 @@ int stls_create(stls_ctx **out, const stls_params *prm, void *cuda_stream) {
     if (!rc && refine) rc = upload(c, &c->a32.band_M[k], to_f32(bM));
     if (!rc && refine) rc = upload(c, &c->a32.band_K[k], to_f32(bK));
     if (!rc && refine) rc = upload(c, &c->a32.band_J[k], to_f32(bJ));
+    if (!rc) rc = upload_padded(c, c->a64, k, D, bM, bK, bJ);
+    if (!rc && refine) rc = upload_padded(c, c->a32, k, D, bM, bK, bJ);
     if (!rc) rc = upload(c, &c->Uf[k], transpose(c->hs.eig_s[k].U, D.n));
     if (!rc) rc = upload(c, &c->Ub[k], c->hs.eig_s[k].U);
   }
@@ -583,6 +631,11 @@ int stls_create(stls_ctx **out, const stls_params *prm, void *cuda_stream) {
     if (!rc) rc = upload(c, &c->a64.band_Mt, bMt);
     if (!rc && refine) rc = upload(c, &c->a32.band_Kt, to_f32(bKt));
     if (!rc && refine) rc = upload(c, &c->a32.band_Mt, to_f32(bMt));
+    const int st64 = stls::band_row_stride(Tm.p, 8), st32 = stls::band_row_stride(Tm.p, 4);
+    if (!rc) rc = upload(c, &c->a64.pad_Kt, pad_band<double>(bKt, Tm.n, Tm.p, st64, 1.0));
+    if (!rc) rc = upload(c, &c->a64.pad_Mt, pad_band<double>(bMt, Tm.n, Tm.p, st64, 1.0));
+    if (!rc && refine) rc = upload(c, &c->a32.pad_Kt, pad_band<float>(bKt, Tm.n, Tm.p, st32, 1.0));
+    if (!rc && refine) rc = upload(c, &c->a32.pad_Mt, pad_band<float>(bMt, Tm.n, Tm.p, st32, 1.0));
   }
   if (!rc) rc = upload(c, &c->Uf[c->d], transpose(c->hs.eig_t.U, Tm.n));
   if (!rc) rc = upload(c, &c->Ub[c->d], c->hs.eig_t.U);

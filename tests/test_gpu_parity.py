@@ -60,6 +60,28 @@ def test_apply_A_matches_oracle(d, p, n_el, T, batch):
         np.testing.assert_allclose(y[b], ref, rtol=0, atol=1e-13 * np.abs(ref).max())
 
 
+# Degree 5, fewer basis functions per direction than the band half-width,
+# and time degrees other than the spatial one: the fused A x kernels take p_s and
+# p_t as template parameters and mask neighbours outside a slice.
+EDGE = [dict(d=2, p=2, n_el=1, T=1.0), dict(d=3, p=2, n_el=2, T=0.8),
+        dict(d=2, p=4, n_el=1, T=1.0), dict(d=3, p=5, n_el=1, T=1.0),
+        dict(d=3, p=3, n_el=[4, 3, 5], T=1.1, p_t=1, n_el_t=7),
+        dict(d=2, p=2, n_el=[6, 9], T=0.5, p_t=5, n_el_t=3)]
+
+
+@pytest.mark.parametrize("cfg", EDGE, ids=lambda c: "-".join(f"{k}{v}" for k, v in c.items()))
+def test_apply_A_edge_cases(cfg):
+    kw = {k: cfg[k] for k in ("p_t", "n_el_t") if k in cfg}
+    prob = STProblem(cfg["d"], cfg["p"], cfg["n_el"], cfg["T"], **kw)
+    S = _solver(cfg["d"], cfg["p"], cfg["n_el"], cfg["T"], batch=2, **kw)
+    x = synth.uniform(prob.N, 31, batch=2).reshape(2, prob.N)
+    y = S.apply_A(_cuda(x)).cpu().numpy().reshape(2, prob.N)
+    A = prob.assemble_A_kron()
+    for b in range(2):
+        ref = A @ x[b]
+        np.testing.assert_allclose(y[b], ref, rtol=0, atol=1e-13 * np.abs(ref).max())
+
+
 def test_apply_A_anisotropic():
     prob = STProblem(3, 3, [3, 5, 4], T=1.7, p_t=2, n_el_t=6)
     S = _solver(3, 3, [3, 5, 4], 1.7, p_t=2, n_el_t=6)
