@@ -7,11 +7,15 @@ One step = one complete solve A u = F from u = 0 to ||r|| / ||F|| <= 1e-8
 direction, N = 18,125,250 unknowns, F ~ U[-1,1] (seed 1809100264).
 
 Metric: solved degrees of freedom per second (DoF/s), whole job.  The
-headline form is the mixed one (BF16 tensor-core preconditioner inside a
-flexible CG, FP64 residual and inner products); the FP64 form is measured on
-the same workload and reported in "fp64_form".
+headline form is the mixed one of this workload: BF16 tensor-core
+preconditioner apply with FP32 accumulation, FP64 outer residual F - A u
+(iterative refinement around a flexible CG in FP32 with FP64-accumulated inner
+products).  The other forms are measured on the same workload in the same run
+and reported under "forms": TF32 refinement, the strict BF16 form (flexible CG
+with FP64 vectors, FP64 A x, only the preconditioner in BF16) and the FP64 PCG.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--precision bf16|tf32|fp64] [--no-refine] [--forms a,b,...]
 
 With --gpus N > 1 (under torchrun) every rank solves its own copy of the
 workload (replicas; the method has no data-path exchange on one node) and
@@ -34,10 +38,14 @@ sys.path.insert(0, ROOT)
 WORKLOAD = dict(name="cube3d_p3_n64", d=3, p=3, n_el=64, T=1.0, tol=1e-8, tag=4,
                 text="3D space + time cube, degree 3, 64 elements per direction, "
                      "N = 18,125,250, F ~ U[-1,1] seed 1809100264, CG tol 1e-8 from u = 0")
-# Iterations of the FP64 PCG on this workload (checked by tests/test_gpu_bench_config.py)
+# Iterations of the FP64 PCG on this workload (measured on the GPU; the CPU
+# baseline extrapolates one oracle iteration by this count)
 FP64_ITERS = 17
 PAPER_DOFS = 18125250 / 227.93  # Table 1, p = 3, n_sub = 64: serial Matlab, i7-5820K (context)
-METRIC = "PCG solve DoF/s (mixed BF16-preconditioned FCG vs FP64 PCG, rel. residual 1e-8)"
+METRIC = "PCG solve DoF/s at relative residual 1e-8 (mixed BF16 form vs FP64 form)"
+# form name -> (precision, refine)
+FORMS = {"bf16_ir": ("bf16", True), "tf32_ir": ("tf32", True), "bf16_fcg": ("bf16", False),
+         "tf32_fcg": ("tf32", False), "fp64_pcg": ("fp64", False)}
 
 
 def load_peaks():
@@ -54,6 +62,8 @@ def load_peaks():
 # FP64 peak: nominal 1.25 TFLOP/s per GB300 (152 SMs); a DFMA probe on this machine
 # measured 1.19 TFLOP/s.
 FP64_PEAK_TFLOPS = 1.25
+# FP32 CUDA-core peak: 152 SMs x 128 FMA/clk x 2 flop x 2.07 GHz (maximum SM clock)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
 class ClockSampler:
@@ -131,13 +141,17 @@ def fd_flops(S):
     return 4.0 * S.N * (sum(S.n_s) + S.n_t) + S.N
 
 
-def apply_A_flops(S, p):
-    # banded products per DoF of the factored A x (3 + 6 + 5 spatial, 2 in time)
-    products = {1: 2 + 2, 2: 3 + 4 + 2, 3: 3 + 6 + 5 + 2}[S.d]
-    return 2.0 * (2 * p + 1) * products * S.N
+def apply_A_flops(S, p, p_t=None):
+    """Banded products per DoF of the fused A x: 3 + 6 (directions 1, 2) + 4
+    (direction 3) + 2 (time) = 15 in three spatial directions, 3 + 4 + 2 = 9 in
+    two; each is 2(2p+1) flops per DoF (the L_s x of the last time slice is
+    not counted)."""
+    p_t = p if p_t is None else p_t
+    spatial = {1: 3, 2: 3 + 4, 3: 3 + 6 + 4}[S.d]
+    return 2.0 * (2 * p + 1) * spatial * S.N + 2.0 * (2 * p_t + 1) * 2 * S.N
 
 
-def timed_solves(S, F, u, tol, steps, warmup, world, device, timing):
+def timed_solves(S, F, u, tol, steps, warmup, world, timing):
     import torch
     for _ in range(warmup):
         S.solve(F, tol, 500, out=u)
@@ -162,29 +176,65 @@ def timed_solves(S, F, u, tol, steps, warmup, world, device, timing):
     return ms, infos, launches, phases
 
 
-def roofline_entry(kind, ms, count, S, p, peaks):
+# ncu DRAM bytes (read + write) per operation on this workload, from the
+# captures summarised under profiles/; None where no capture of the current
+# kernels exists.
+TRAFFIC = {}
+
+
+def roofline_entry(phase, ms, count, S, p, peaks, refine):
+    """Roofline of one operation (the kernels between two phase events), from
+    the CUDA-event phase times of the timed solves."""
     if count == 0 or ms <= 0:
         return None
     per = ms / count * 1e-3
-    if kind == "precond_fp64":
+    hbm = peaks["hbm_gbs"]
+    src = peaks["source"] + " hbm_gbs"
+    if phase == "precond" and S.precision == "fp64":
         ach = fd_flops(S) / per / 1e12
-        return {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "FD apply (FP64 mode products)",
-                "peak_source": "nominal FP64 (1.25 TFLOP/s)", "avg_ms": per * 1e3}
-    if kind == "precond_mixed":
-        ach = 16.0 * S.N / per / 1e9
-        return {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / peaks["hbm_gbs"], "traffic": None,
-                "kernel": "FD apply (tensor-core mode products)",
-                "peak_source": peaks["source"] + " hbm_gbs", "avg_ms": per * 1e3}
-    if kind == "apply_A":
+        e = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+             "kernel": "FD apply, FP64 mode products", "peak_source": "nominal FP64 1.25 TFLOP/s"}
+    elif phase == "precond":
+        # vectors in and out: FP32 inside the refinement form, FP64 in the strict form
+        nbytes = (8.0 if refine else 16.0) * S.N
+        ach = nbytes / per / 1e9
+        e = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+             "kernel": "FD apply, %s tensor-core mode products (%s in/out)"
+                       % (S.precision, "FP32" if refine else "FP64"),
+             "algorithmic_bytes": nbytes, "peak_source": src}
+    elif phase == "apply_A":
         ach = apply_A_flops(S, p) / per / 1e12
-        return {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "A x (FP64 banded mode products)",
-                "peak_source": "nominal FP64 (1.25 TFLOP/s)", "avg_ms": per * 1e3}
-    if kind == "cg_vectors":
+        e = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+             "kernel": "A x, FP64 fused banded mode products", "peak_source": "nominal FP64 1.25 TFLOP/s"}
+    elif phase == "apply_A_f32":
+        ach = apply_A_flops(S, p) / per / 1e12
+        e = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+             "kernel": "A x, FP32 fused banded mode products",
+             "peak_source": "FP32 FMA units x max SM clock (152 x 128 x 2 x 2.07 GHz)"}
+    else:
         return None
-    return None
+    e["frac"] = e["achieved"] / e["peak"]
+    e["traffic"] = TRAFFIC.get((phase, S.precision, refine))
+    e["avg_ms"] = per * 1e3
+    e["launch_ops"] = count
+    return e
+
+
+def run_form(stls, name, W, F, args, world, sampler=None):
+    import torch
+    precision, refine = FORMS[name]
+    S = stls.Solver(W["d"], W["p"], W["n_el"], W["T"], precision=precision, refine=refine,
+                    device=F.device)
+    u = torch.empty_like(F)
+    steps = args.steps if sampler is not None else max(1, min(args.steps, args.form_steps))
+    if sampler is not None:
+        sampler.start()
+    ms, infos, launches, _ = timed_solves(S, F, u, W["tol"], steps, args.warmup, world, False)
+    clocks = sampler.stop() if sampler is not None else None
+    ms_max = max_over_ranks(ms, world, F.device)
+    _, _, _, phases = timed_solves(S, F, u, W["tol"], 1, 0, world, True)
+    return dict(S=S, u=u, ms=ms_max, infos=infos, launches=launches, phases=phases, steps=steps,
+                clocks=clocks, precision=precision, refine=refine)
 
 
 def cpu_baseline_sample(F, iters):
@@ -217,7 +267,6 @@ def cpu_baseline_sample(F, iters):
 
 
 def run_ours(args):
-    import numpy as np
     import torch
     import paper_1809_10026_gb300 as stls
     from paper_1809_10026_gb300 import synth
@@ -227,39 +276,25 @@ def run_ours(args):
     device = torch.device("cuda", local)
     peaks = load_peaks()
     W = WORKLOAD
-    forms = [args.precision]
-    if args.precision != "fp64":
-        forms.append("fp64")
+    head = args.precision + ("_ir" if (args.precision != "fp64" and not args.no_refine) else
+                             ("_fcg" if args.precision != "fp64" else "_pcg"))
+    extra = [f for f in args.forms.split(",") if f and f != head] if args.forms else []
+    for f in extra:
+        if f not in FORMS:
+            raise SystemExit("unknown form %r (known: %s)" % (f, ", ".join(FORMS)))
     F_host = synth.uniform(18125250, W["tag"])
     F = torch.from_numpy(F_host).to(device)
-    results = {}
-    sampler = ClockSampler(local)
-    for form in forms:
-        S = stls.Solver(W["d"], W["p"], W["n_el"], W["T"], precision=form, device=device)
-        u = torch.empty_like(F)
-        steps = args.steps if form == forms[0] else max(1, min(args.steps, args.fp64_steps))
-        if form == forms[0]:
-            sampler.start()
-        ms, infos, launches, _ = timed_solves(S, F, u, W["tol"], steps, args.warmup, world, device, False)
-        if form == forms[0]:
-            clocks = sampler.stop()
-        ms_max = max_over_ranks(ms, world, device)
-        _, _, _, phases = timed_solves(S, F, u, W["tol"], steps, 0, world, device, True)
-        results[form] = dict(S=S, u=u, ms=ms_max, infos=infos, launches=launches, phases=phases,
-                             steps=steps)
-    main = results[forms[0]]
+    main = run_form(stls, head, W, F, args, world, sampler=ClockSampler(local))
     S = main["S"]
     N = S.N
-    value = N * main["steps"] * world / (main["ms"] * 1e-3)
-    # roofline: dominant phase of the headline form, and the preconditioner apply
-    ph = main["phases"]
     p = W["p"]
-    pre_kind = "precond_fp64" if forms[0] == "fp64" else "precond_mixed"
-    entries = {"precond": roofline_entry(pre_kind, ph["precond"][0], ph["precond"][1], S, p, peaks),
-               "apply_A": roofline_entry("apply_A", ph["apply_A"][0], ph["apply_A"][1], S, p, peaks)}
-    dominant = max(("precond", "apply_A"), key=lambda k: ph[k][0])
+    value = N * main["steps"] * world / (main["ms"] * 1e-3)
+    ph = main["phases"]
+    entries = {k: roofline_entry(k, v[0], v[1], S, p, peaks, main["refine"]) for k, v in ph.items()}
     total_ph = sum(v[0] for v in ph.values())
-    # end to end through the host-pointer C entry point (pinned host buffers)
+    dominant = max((k for k in ph if entries.get(k)), key=lambda k: ph[k][0])
+    # end to end through the host-pointer C entry point (pinned host buffers,
+    # H2D of F and D2H of u inside the timed region)
     Fh = torch.from_numpy(F_host).pin_memory()
     uh = torch.empty_like(Fh).pin_memory()
     for _ in range(args.warmup):
@@ -283,35 +318,43 @@ def run_ours(args):
         "ms_per_step": main["ms"] / main["steps"],
         "higher_is_better": True,
         "scaling": "weak",
-        "vs_baseline": value / PAPER_DOFS,
-        "dtype": "f64" if forms[0] == "fp64" else forms[0] + "+f64",
+        "vs_baseline": None,
+        "dtype": {"bf16_ir": "bf16+f32+f64", "tf32_ir": "tf32+f32+f64", "bf16_fcg": "bf16+f64",
+                  "tf32_fcg": "tf32+f64", "fp64_pcg": "f64"}[head],
         "data": "synthetic",
-        "config": {"workload": W["name"], "description": W["text"], "form": forms[0],
+        "config": {"workload": W["name"], "description": W["text"], "form": head,
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (145 MB FP64 vectors, 129 MB L2)",
-                   "iterations": it["iters"], "true_rel_res": it["true_rel_res"]},
-        "roofline": dict(entries[dominant] or {}, phase=dominant,
+                   "iterations": it["iters"], "outer": it["outer"], "true_rel_res": it["true_rel_res"]},
+        "roofline": dict(entries[dominant], phase=dominant,
                          phase_share=ph[dominant][0] / total_ph if total_ph else None),
-        "precond_roofline": entries["precond"],
-        "phase_ms_per_solve": {k: v[0] / main["steps"] for k, v in ph.items()},
+        "precond_roofline": entries.get("precond"),
+        "phase_ms_per_solve": {k: v[0] for k, v in ph.items()},
+        "phase_calls_per_solve": {k: v[1] for k, v in ph.items()},
         "e2e": {"value": N * main["steps"] * world / e2e_s, "unit": "DoF/s",
                 "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N},
         "gpu_launches": main["launches"],
-        "clocks": clocks,
-        "paper_context": {"dofs": PAPER_DOFS, "note": "Table 1, p=3, n_sub=64: 13 it / 227.93 s, serial "
-                                                      "Matlab FP64 on i7-5820K incl. setup, manufactured RHS"},
+        "clocks": main["clocks"],
+        "paper_context": {"dofs_per_s": PAPER_DOFS,
+                          "note": "Table 1, p=3, n_sub=64: 13 iterations / 227.93 s, serial Matlab FP64 "
+                                  "on an i7-5820K incl. setup, manufactured right-hand side"},
     }
-    if "fp64" in results and forms[0] != "fp64":
-        r64 = results["fp64"]
-        S64 = r64["S"]
-        ph64 = r64["phases"]
-        line["fp64_form"] = {"value": N * r64["steps"] * world / (r64["ms"] * 1e-3), "unit": "DoF/s",
-                             "ms_per_step": r64["ms"] / r64["steps"], "steps": r64["steps"],
-                             "iterations": r64["infos"][-1]["iters"],
-                             "precond_roofline": roofline_entry("precond_fp64", ph64["precond"][0],
-                                                                ph64["precond"][1], S64, p, peaks),
-                             "apply_A_roofline": roofline_entry("apply_A", ph64["apply_A"][0],
-                                                                ph64["apply_A"][1], S64, p, peaks)}
+    forms = {}
+    for name in extra:
+        r = run_form(stls, name, W, F, args, world)
+        Sx, phx = r["S"], r["phases"]
+        forms[name] = {"value": N * r["steps"] * world / (r["ms"] * 1e-3), "unit": "DoF/s",
+                       "ms_per_step": r["ms"] / r["steps"], "steps": r["steps"],
+                       "iterations": r["infos"][-1]["iters"], "outer": r["infos"][-1]["outer"],
+                       "true_rel_res": r["infos"][-1]["true_rel_res"], "gpu_launches": r["launches"],
+                       "phase_ms_per_solve": {k: v[0] for k, v in phx.items()},
+                       "rooflines": {k: roofline_entry(k, v[0], v[1], Sx, p, peaks, r["refine"])
+                                     for k, v in phx.items() if v[1]}}
+        Sx.close()
+        del r
+        torch.cuda.empty_cache()
+    if forms:
+        line["forms"] = forms
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample(F_host, FP64_ITERS)
     if rank == 0:
@@ -393,7 +436,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp64", "tf32", "bf16"], default="bf16")
-    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--no-refine", action="store_true",
+                    help="headline mixed form without the FP64 outer residual (strict flexible CG)")
+    ap.add_argument("--forms", default="tf32_ir,bf16_fcg,fp64_pcg",
+                    help="other forms timed in the same run (comma separated; empty for none)")
+    ap.add_argument("--form-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
