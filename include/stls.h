@@ -73,7 +73,11 @@ typedef struct {
                        (FP32 vectors and A p, tensor-core preconditioner, inner
                        products accumulated in FP64) that reduces its scaled
                        residual by inner_tol. */
-  double inner_tol; /* relative tolerance of the inner solves (0: 1e-4) */
+  double inner_tol; /* relative tolerance of the inner solves.  0: adaptive:
+                       the reduction R = tol ||F|| / ||r|| still needed is split
+                       over K = ceil(log R / log 1e-3) outer steps, inner
+                       tolerance R^(1/K) clamped to [1e-4, 0.1]; at most 400
+                       inner iterations per outer step */
 } stls_params;
 
 typedef struct {

@@ -453,8 +453,16 @@ int solve_ir_impl(stls_ctx *c, const double *F, double *u, double tol, int maxit
   if (check_ptr(c, F, "F") || check_ptr(c, u, "u")) return STLS_EINVAL;
   const long long N = c->N;
   const int B = c->B;
-  const double eta = c->hs.prm.inner_tol > 0.0 ? c->hs.prm.inner_tol : 1e-4;
-  const int kMaxOuter = 100;
+  // Inner target: fixed inner_tol when given.  Otherwise: one outer step
+  // reduces the FP64 residual by about max(eta, 4e-4) (the FP32 inner operator
+  // bounds the contraction), so the reduction R = tol / (||r|| / ||F||) still
+  // needed by the worst right-hand side is split evenly over the
+  // K = ceil(log R / log 1e-3) steps it takes: eta = R^(1/K), at least 1e-4.
+  // A cap on inner iterations per outer step stops an inner solve that
+  // stagnates; the FP64 outer residual decides convergence.
+  const bool adaptive = !(c->hs.prm.inner_tol > 0.0);
+  const double eta_fixed = c->hs.prm.inner_tol, eta_min = 1e-4, kStep = 1e-3;
+  const int kMaxOuter = 100, kMaxInnerPerOuter = 400;
   double *r64 = c->r, *q64 = c->q;
   int ph = phase_begin(c, 2);
   STLS_LAUNCH(stls::launch_cg_init(F, u, r64, N, B, c->st, c->rw, c->stream), "cg_init");
@@ -466,8 +474,23 @@ int solve_ir_impl(stls_ctx *c, const double *F, double *u, double tol, int maxit
             "state copy");
     STLS_CK(cudaStreamSynchronize(c->stream), "sync");
     bool any = false;
-    for (int b = 0; b < B; ++b) any = any || c->st_host[b].active;
+    double worst = 0.0;
+    for (int b = 0; b < B; ++b)
+      if (c->st_host[b].active) {
+        any = true;
+        worst = std::max(worst, c->st_host[b].rel_res);
+      }
     if (!any || total_inner >= maxit) break;
+    double eta = eta_fixed;
+    if (adaptive) {
+      const double R = (worst > 0.0 && tol > 0.0) ? std::min(1.0, tol / worst) : 0.0;
+      if (R <= 0.0) {
+        eta = eta_min;
+      } else {
+        const int K = std::max(1, static_cast<int>(std::ceil(std::log(R) / std::log(kStep) - 1e-9)));
+        eta = std::min(0.1, std::max(eta_min, std::pow(R, 1.0 / K)));
+      }
+    }
     // ---- inner flexible CG in FP32 on A d = r / ||r|| ----
     ph = phase_begin(c, 2);
     STLS_LAUNCH(stls::launch_ir_start(r64, c->ri, c->di, N, B, c->st, c->st_in, c->rw, c->stream), "ir_start");
@@ -481,7 +504,7 @@ int solve_ir_impl(stls_ctx *c, const double *F, double *u, double tol, int maxit
                 "cg_beta");
     STLS_LAUNCH(stls::launch_cg_p<float>(c->zi, c->pi, N, B, 1, c->st_in, c->stream), "cg_p");
     phase_end(c, ph);
-    const int budget = maxit - total_inner;
+    const int budget = std::min(maxit - total_inner, kMaxInnerPerOuter);
     for (int it = 1; it <= budget; ++it) {
       ph = phase_begin(c, 3);
       rc = apply_A_impl<float>(c, c->a32, c->pi, c->qi);

@@ -27,8 +27,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=2)
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--refine", action="store_true", help="iterative-refinement form (mixed precisions)")
+    ap.add_argument("--inner-tol", type=float, default=0.0, help="inner tolerance of the refinement form (0: adaptive)")
     a = ap.parse_args()
-    S = stls.Solver(a.d, a.p, a.n_el, precision=a.precision, batch=a.batch, refine=a.refine)
+    S = stls.Solver(a.d, a.p, a.n_el, precision=a.precision, batch=a.batch, refine=a.refine,
+                    inner_tol=a.inner_tol)
     x = torch.from_numpy(synth.uniform(S.N, 4, batch=a.batch)).cuda()
     y = torch.empty_like(x)
 
@@ -61,7 +63,8 @@ def main():
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / a.reps
-    out = {"op": a.op, "precision": a.precision, "refine": a.refine, "N": S.N, "batch": a.batch, "ms": ms,
+    out = {"op": a.op, "precision": a.precision, "refine": a.refine, "inner_tol": a.inner_tol, "N": S.N,
+           "batch": a.batch, "ms": ms,
            "launches_per_rep": (S.launch_count() - l0) / a.reps}
     if info is not None:
         out["info"] = info[0]
