@@ -119,6 +119,15 @@ int stls_apply_A(stls_ctx *ctx, const double *x, double *y);
  * r == z is allowed. */
 int stls_apply_precond(stls_ctx *ctx, const double *r, double *z);
 
+/* Operand rounding of the BF16 preconditioner (the mixed form of Algorithm 1,
+ * step 2): y[i] = x[i] rounded to FP32, then to BF16, both to nearest with
+ * ties to even, returned exactly as FP64.  This is how the BF16 form rounds
+ * its FP64 input r before the first mode product.  x, y: device, n entries
+ * (x == y allowed), n >= 0; ordered on `cuda_stream` (NULL = legacy default
+ * stream), asynchronous.  Needs no context.  Errors: STLS_EINVAL (n < 0, NULL
+ * pointer with n > 0), STLS_ECUDA; text via stls_last_error(NULL). */
+int stls_round_bf16(const double *x, double *y, long long n, void *cuda_stream);
+
 /* Solve A u = F for the batch by (flexible) preconditioned CG from u = 0,
  * stopping each right-hand side when ||r_k|| / ||F|| <= tol (Sec. 5: tolerance
  * on the relative residual, zero initial guess).  With refine = 1, maxit bounds

@@ -8,6 +8,16 @@ accumulation; intermediate tensors are stored in BF16 (BF16 form) or FP32
 eigenvalues rounded to FP32; the input r is FP64 and is rounded to FP32 and
 then to the operand format; the output is the FP32 accumulator widened to FP64.
 
+Order of the products.  Algorithm 1 applies Kronecker products of the 1D
+eigenvector matrices, i.e. d+1 mode products that act on different tensor
+directions and commute in exact arithmetic, so the algorithm fixes no order;
+with a rounding after every product the order matters at the level of the
+rounding error.  The forward products always run in the order 1, ..., d, t
+(the division needs the time product last).  ``bwd_order="ascending"``
+applies the backward products in the order 1, ..., d, t;
+``bwd_order="descending"`` in the order t, d, ..., 1 (the fused tensor-core
+kernels of the BF16 form for d = 2, 3 run this order).
+
 This model applies the same roundings with numpy: every operand is rounded
 where the method rounds it, and every product is accumulated in FP64 and then
 rounded to FP32.  It differs from any FP32 tensor-core accumulation only by
@@ -36,7 +46,7 @@ def round_tf32(x):
     return b.view(np.float32)
 
 
-def apply_mixed(fd, r, form):
+def apply_mixed(fd, r, form, bwd_order="ascending"):
     """z ~ P^{-1} r with the roundings of the mixed form ("bf16" or "tf32")."""
     prob = fd.prob
     d = prob.d
@@ -52,6 +62,10 @@ def apply_mixed(fd, r, form):
     modes_bwd = [(k + 1, fd.U[k]) for k in range(d)] + [(d + 1, fd.U_t)]
     lam_t = f32(fd.lam_t)
     lam_s = [f32(l) for l in fd.lam]
+    if bwd_order == "descending":
+        modes_bwd = modes_bwd[::-1]
+    elif bwd_order != "ascending":
+        raise ValueError("bwd_order must be 'ascending' or 'descending'")
     steps = [(k, W, False) for k, W in modes_fwd] + [(k, W, True) for k, W in modes_bwd]
     for idx, (k, W, bwd) in enumerate(steps):
         Wq = q_op(W).astype(np.float64)

@@ -12,7 +12,7 @@ import numpy as np
 from . import _lib
 from ._lib import FACTOR, make_params
 
-__all__ = ["Solver", "SolveFn", "host_factor", "make_params"]
+__all__ = ["Solver", "SolveFn", "host_factor", "make_params", "round_bf16"]
 
 
 def _check(rc, ctx=None):
@@ -34,6 +34,21 @@ def host_factor(which, direction, d, p, n_el, **kw):
                               out.ctypes.data_as(ctypes.c_void_p))
     _check(rc)
     return out if size == n else out.reshape(n, n)
+
+
+def round_bf16(x):
+    """FP64(BF16(FP32(x))) elementwise on the GPU (stls_round_bf16): the operand
+    rounding of the BF16 preconditioner.  x: CUDA float64 tensor."""
+    import torch
+    if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float64):
+        raise TypeError("round_bf16 expects a CUDA float64 tensor")
+    x = x.contiguous()
+    y = torch.empty_like(x)
+    lib = _lib.load()
+    rc = lib.stls_round_bf16(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), x.numel(),
+                             ctypes.c_void_p(torch.cuda.current_stream(x.device).cuda_stream))
+    _check(rc)
+    return y
 
 
 class Solver:

@@ -712,16 +712,18 @@ int stls_create(stls_ctx **out, const stls_params *prm, void *cuda_stream) {
     return fail(STLS_ECUDA);
   }
   if (P.precision != STLS_FP64) {
-    std::vector<std::vector<double>> U(c->d + 1);
+    std::vector<std::vector<double>> U(c->d + 1), lam(c->d + 1);
     std::vector<int> n(c->d + 1);
     for (int k = 0; k < c->d; ++k) {
       U[k] = c->hs.eig_s[k].U;
+      lam[k] = c->hs.eig_s[k].lam;
       n[k] = c->n_s[k];
     }
     U[c->d] = c->hs.eig_t.U;
+    lam[c->d] = c->hs.eig_t.lam;
     n[c->d] = c->n_t;
     std::string tcerr;
-    cudaError_t e = stls::tc_fd_create(c->tc, P.precision, c->d, n.data(), c->B, U, c->lam_t, c->lam_s,
+    cudaError_t e = stls::tc_fd_create(c->tc, P.precision, c->d, n.data(), c->B, U, lam, c->lam_t, c->lam_s,
                                        tcerr);
     if (e != cudaSuccess || !tcerr.empty()) {
       c->err = tcerr.empty() ? std::string("tensor-core FD setup: ") + cudaGetErrorString(e) : tcerr;
@@ -782,6 +784,19 @@ int stls_solve_host(stls_ctx *c, const double *F_host, double *u_host, double to
   STLS_CK(cudaMemcpyAsync(u_host, c->du, bytes, cudaMemcpyDeviceToHost, c->stream), "D2H copy of u");
   STLS_CK(cudaStreamSynchronize(c->stream), "sync");
   return rc;
+}
+
+int stls_round_bf16(const double *x, double *y, long long n, void *cuda_stream) {
+  if (n < 0 || (n > 0 && (x == nullptr || y == nullptr))) {
+    g_create_error = "stls_round_bf16: n < 0 or NULL pointer";
+    return STLS_EINVAL;
+  }
+  cudaError_t e = stls::round_bf16_launch(x, y, n, static_cast<cudaStream_t>(cuda_stream));
+  if (e != cudaSuccess) {
+    g_create_error = std::string("stls_round_bf16: ") + cudaGetErrorString(e);
+    return STLS_ECUDA;
+  }
+  return STLS_OK;
 }
 
 int stls_apply_lift(stls_ctx *c, const double *c0, double *y) {

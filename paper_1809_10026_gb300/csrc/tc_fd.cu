@@ -403,8 +403,8 @@ cudaError_t dev_alloc(TcFd &tc, T **p, size_t count) {
 }  // namespace
 
 cudaError_t tc_fd_create(TcFd &tc, int precision, int d, const int *n, int B,
-                         const std::vector<std::vector<double>> &U, const double *lam_t_dev,
-                         const double *lam_s_dev, std::string &err) {
+                         const std::vector<std::vector<double>> &U, const std::vector<std::vector<double>> &lam,
+                         const double *lam_t_dev, const double *lam_s_dev, std::string &err) {
   tc.precision = precision;
   tc.d = d;
   tc.B = B;
@@ -427,6 +427,16 @@ cudaError_t tc_fd_create(TcFd &tc, int precision, int d, const int *n, int B,
   if (major != 10 || minor != 3) {
     err = "the tensor-core preconditioner needs an sm_103 (GB300) device";
     return cudaSuccess;
+  }
+  if ((e = cudaHostAlloc(reinterpret_cast<void **>(&im->err_host), sizeof(int), cudaHostAllocMapped)) != cudaSuccess)
+    return e;
+  *im->err_host = 0;
+  if ((e = cudaHostGetDevicePointer(reinterpret_cast<void **>(&im->err_dev), im->err_host, 0)) != cudaSuccess)
+    return e;
+  if (tc_fd_fused_eligible(precision, d, n)) {
+    e = tc_fd_fused_create(tc.fused, tc.allocations, d, n, B, U, lam, im->err_dev, err);
+    if (e == cudaSuccess && err.empty()) tc.launches_per_apply = tc_fd_fused_launches(tc.fused);
+    return e;
   }
   for (int k = 0; k <= d; ++k) {
     Mode &m = im->mode[k];
@@ -465,11 +475,6 @@ cudaError_t tc_fd_create(TcFd &tc, int precision, int d, const int *n, int B,
   if ((e = dev_alloc(tc, &im->lam_s, lsf.size())) != cudaSuccess) return e;
   if ((e = cudaMemcpy(im->lam_t, ltf.data(), 4 * ltf.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
   if ((e = cudaMemcpy(im->lam_s, lsf.data(), 4 * lsf.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
-  if ((e = cudaHostAlloc(reinterpret_cast<void **>(&im->err_host), sizeof(int), cudaHostAllocMapped)) != cudaSuccess)
-    return e;
-  *im->err_host = 0;
-  if ((e = cudaHostGetDevicePointer(reinterpret_cast<void **>(&im->err_dev), im->err_host, 0)) != cudaSuccess)
-    return e;
   tc.launches_per_apply = 2 * (d + 1);
   return cudaSuccess;
 }
@@ -533,9 +538,15 @@ cudaError_t apply_passes(TcFd &tc, const IO *r, IO *z, cudaStream_t s) {
 
 }  // namespace
 
-cudaError_t tc_fd_apply(TcFd &tc, const double *r, double *z, cudaStream_t s) { return apply_passes<double>(tc, r, z, s); }
+cudaError_t tc_fd_apply(TcFd &tc, const double *r, double *z, cudaStream_t s) {
+  if (tc.fused != nullptr) return tc_fd_fused_apply<double>(tc.fused, r, z, s);
+  return apply_passes<double>(tc, r, z, s);
+}
 
-cudaError_t tc_fd_apply_f32(TcFd &tc, const float *r, float *z, cudaStream_t s) { return apply_passes<float>(tc, r, z, s); }
+cudaError_t tc_fd_apply_f32(TcFd &tc, const float *r, float *z, cudaStream_t s) {
+  if (tc.fused != nullptr) return tc_fd_fused_apply<float>(tc.fused, r, z, s);
+  return apply_passes<float>(tc, r, z, s);
+}
 
 int tc_fd_error(const TcFd &tc) {
   const Impl *im = static_cast<const Impl *>(tc.impl);
@@ -545,6 +556,8 @@ int tc_fd_error(const TcFd &tc) {
 int tc_fd_launch_count(const TcFd &tc) { return tc.launches_per_apply; }
 
 void tc_fd_destroy(TcFd &tc) {
+  if (tc.fused != nullptr) tc_fd_fused_destroy(tc.fused);
+  tc.fused = nullptr;
   for (void *p : tc.allocations) cudaFree(p);
   tc.allocations.clear();
   Impl *im = static_cast<Impl *>(tc.impl);

@@ -11,6 +11,8 @@
 
 namespace stls {
 
+struct FusedFd;
+
 struct TcFd {
   int precision = 0, d = 0, B = 0;
   int n[4] = {0, 0, 0, 0};
@@ -18,14 +20,17 @@ struct TcFd {
   int launches_per_apply = 0;
   std::vector<void *> allocations;
   void *impl = nullptr;
+  FusedFd *fused = nullptr;  // BF16, d = 2, 3: fused passes (tc_fd_fused.cu)
 };
 
 // U[k] (row-major n[k] x n[k], k = 0..d-1 space, d = time) are the FP64
-// eigenvector matrices; lam_t_dev / lam_s_dev are device arrays of the time
-// eigenvalues and the summed spatial eigenvalues (length N_s).
+// eigenvector matrices and lam[k] their eigenvalues; lam_t_dev / lam_s_dev are
+// device arrays of the time eigenvalues and the summed spatial eigenvalues
+// (length N_s).  BF16 with d = 2 or 3 and every n[k] <= 128 uses the fused
+// passes; other cases one launch per mode product.
 cudaError_t tc_fd_create(TcFd &tc, int precision, int d, const int *n, int B,
-                         const std::vector<std::vector<double>> &U, const double *lam_t_dev,
-                         const double *lam_s_dev, std::string &err);
+                         const std::vector<std::vector<double>> &U, const std::vector<std::vector<double>> &lam,
+                         const double *lam_t_dev, const double *lam_s_dev, std::string &err);
 cudaError_t tc_fd_apply(TcFd &tc, const double *r, double *z, cudaStream_t s);
 // Same with FP32 r and z (inner solves of the refinement form).
 cudaError_t tc_fd_apply_f32(TcFd &tc, const float *r, float *z, cudaStream_t s);
@@ -34,5 +39,17 @@ int tc_fd_launch_count(const TcFd &tc);
 // flag; read it after synchronizing the stream).
 int tc_fd_error(const TcFd &tc);
 void tc_fd_destroy(TcFd &tc);
+
+// Fused BF16 passes (slab and streaming kernels), tc_fd_fused.cu.
+bool tc_fd_fused_eligible(int precision, int d, const int *n);
+cudaError_t tc_fd_fused_create(FusedFd *&out, std::vector<void *> &allocs, int d, const int *n, int B,
+                               const std::vector<std::vector<double>> &U, const std::vector<std::vector<double>> &lam,
+                               int *err_dev, std::string &err);
+template <typename IO>
+cudaError_t tc_fd_fused_apply(FusedFd *f, const IO *r, IO *z, cudaStream_t s);
+int tc_fd_fused_launches(const FusedFd *f);
+void tc_fd_fused_destroy(FusedFd *f);
+// y = FP64(BF16(FP32(x))), both roundings to nearest even, as the fused kernels round r.
+cudaError_t round_bf16_launch(const double *x, double *y, long long n, cudaStream_t s);
 
 }  // namespace stls

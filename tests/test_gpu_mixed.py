@@ -36,20 +36,61 @@ def _rel(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
+def _bwd_order(form, d):
+    # the fused BF16 kernels (d = 2, 3) run the backward products as t, d, ..., 1
+    return "descending" if form == "bf16" and d >= 2 else "ascending"
+
+
 @pytest.mark.parametrize("form", ["bf16", "tf32"])
 @pytest.mark.parametrize("d,p,n_el,batch", [(1, 2, 7, 1), (2, 3, 6, 3), (2, 5, 9, 1), (3, 2, 4, 2),
-                                            (3, 3, 9, 1), (3, 4, 12, 1)])
+                                            (3, 3, 9, 1), (3, 4, 12, 1), (2, 2, 70, 2), (3, 3, 20, 2),
+                                            (3, 2, 1, 1)])
 def test_tc_precond_matches_model(form, d, p, n_el, batch):
+    """Several slab steps and streaming tiles with ragged tails, odd sizes (n = 2..71),
+    batches, and the smallest mesh (one element)."""
     prob = STProblem(d, p, n_el)
     fd = FD(prob)
     S = _solver(d, p, n_el, precision=form, batch=batch)
     r = synth.uniform(prob.N, 500 + d + p, batch=batch).reshape(batch, prob.N)
     z = S.apply_precond(torch.from_numpy(r).cuda()).cpu().numpy().reshape(batch, prob.N)
     for b in range(batch):
-        model = mixed.apply_mixed(fd, r[b], form)
+        model = mixed.apply_mixed(fd, r[b], form, _bwd_order(form, d))
         exact = fd.apply(r[b])
         assert _rel(z[b], model) <= TOL_MODEL[form], (_rel(z[b], model), _rel(z[b], exact))
         assert _rel(z[b], exact) <= TOL_EXACT[form]
+
+
+def test_operand_rounding_bit_exact():
+    """FP64 -> FP32 -> BF16 rounding of the BF16 preconditioner's input (integer
+    implementation on the GPU) equals numpy's IEEE rounding bit for bit: random
+    values over the whole exponent range, exact FP64 -> FP32 and FP32 -> BF16 ties,
+    the FP32 overflow threshold, FP32 subnormals, FP64 subnormals, signed zeros,
+    infinities and NaN."""
+    import paper_1809_10026_gb300 as stls
+    rng = np.random.default_rng(1809)
+    parts = [rng.standard_normal(100000) * np.exp2(rng.integers(-160, 140, 100000)).astype(np.float64)]
+    # exact halfway points between neighbouring FP32 values (even and odd kept parts)
+    f32 = rng.standard_normal(20000).astype(np.float32)
+    f = f32.astype(np.float64)
+    half32 = np.spacing(f32).astype(np.float64) / 2
+    parts += [f + half32, f - half32 / 2, f + half32 * (1 - 2.0 ** -20)]
+    # exact halfway points between neighbouring BF16 values
+    b = mixed.round_bf16(rng.standard_normal(20000).astype(np.float32)).astype(np.float64)
+    _, ex = np.frexp(b)
+    half16 = np.ldexp(np.sign(b), ex - 9)
+    parts += [b + half16, b - half16, b + half16 * 3]
+    fmax = float(np.finfo(np.float32).max)
+    parts.append(np.array([0.0, -0.0, np.inf, -np.inf, np.nan, fmax, -fmax, fmax * (1 + 2.0 ** -25),
+                           fmax * (1 + 2.0 ** -24), 2.0 ** -126, 2.0 ** -130, 2.0 ** -149, 2.0 ** -150,
+                           3 * 2.0 ** -151, 5e-324, -5e-324, 1e-310, 1.0, -1.0, 1 + 2.0 ** -24,
+                           1 + 3 * 2.0 ** -24, 2.0 ** 128, 1e300, -1e300]))
+    x = np.concatenate(parts)
+    with np.errstate(over="ignore"):
+        want = mixed.round_bf16(x.astype(np.float32)).astype(np.float64)
+    got = stls.round_bf16(torch.from_numpy(x).cuda()).cpu().numpy()
+    nan = np.isnan(want)
+    assert np.array_equal(np.isnan(got), nan)
+    assert np.array_equal(got[~nan].view(np.uint64), want[~nan].view(np.uint64))
 
 
 @pytest.mark.parametrize("form", ["bf16", "tf32"])

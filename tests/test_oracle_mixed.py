@@ -1,5 +1,6 @@
 """Pins for oracle.mixed: rounding helpers and the identity-rounding limit."""
 import numpy as np
+import pytest
 
 from oracle import mixed
 from oracle.fd import FD
@@ -38,8 +39,27 @@ def test_mixed_model_close_to_fp64_and_ordered():
     assert e_tf < 5e-3
 
 
-def test_identity_rounding_is_algorithm_1():
+@pytest.mark.parametrize("bwd_order", ["ascending", "descending"])
+def test_identity_rounding_is_algorithm_1(bwd_order):
     prob = STProblem(3, 2, 3)
     fd = FD(prob)
     r = np.random.default_rng(4).uniform(-1, 1, prob.N)
-    np.testing.assert_allclose(mixed.apply_mixed(fd, r, "fp64"), fd.apply(r), rtol=1e-13, atol=1e-14)
+    np.testing.assert_allclose(mixed.apply_mixed(fd, r, "fp64", bwd_order), fd.apply(r), rtol=1e-13, atol=1e-14)
+
+
+def test_backward_order_changes_only_roundings():
+    """Both orders are Algorithm 1 with different rounding points: their BF16 results
+    differ from each other by about the model's own rounding error, and each is within
+    the BF16 bound of the exact solve."""
+    prob = STProblem(2, 3, 5)
+    fd = FD(prob)
+    r = np.random.default_rng(5).uniform(-1, 1, prob.N)
+    z = fd.apply(r)
+    za = mixed.apply_mixed(fd, r, "bf16", "ascending")
+    zd = mixed.apply_mixed(fd, r, "bf16", "descending")
+    ea = np.linalg.norm(za - z) / np.linalg.norm(z)
+    ed = np.linalg.norm(zd - z) / np.linalg.norm(z)
+    assert ea < 5e-2 and ed < 5e-2
+    assert 0 < np.linalg.norm(za - zd) / np.linalg.norm(z) < 5e-2
+    with pytest.raises(ValueError):
+        mixed.apply_mixed(fd, r, "bf16", "sideways")
