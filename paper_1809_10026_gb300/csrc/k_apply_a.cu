@@ -17,6 +17,8 @@
 // direction needs M_s x = M3 m, J_s x = M3 j' + J3 m + 2 K3 k, L_s x = M3 k + K3 m:
 // 15 banded products per unknown in three spatial directions, each band row
 // multiplied once.
+#include <cstring>
+
 #include "kernels.h"
 
 namespace stls {
@@ -97,105 +99,164 @@ constexpr int prefetch_rows() {
   return sizeof(T) == 4 ? 8 : 4;
 }
 
+// Coefficients of band row i: the interior copy `in` when i lies in [lo, hi),
+// else loaded from the band array (the few boundary rows).
+template <typename T, int W>
+__device__ __forceinline__ void band_row(const T *__restrict__ band, int i, int wp, int lo, int hi,
+                                         const T (&in)[W], T (&c)[W]) {
+  if (i >= lo && i < hi) {
+#pragma unroll
+    for (int w = 0; w < W; ++w) c[w] = in[w];
+  } else {
+    load_row<T, W>(band + static_cast<size_t>(i) * wp, c);
+  }
+}
+
 // ---- directions 1 and 2 --------------------------------------------------------------
-// Columns are the (slice, i_1) pairs in order; a CTA owns kAThreads consecutive
-// columns and walks i_2.  Each row i_2 of the CTA's columns (plus P columns of
-// halo on each side) is staged in shared memory; every thread forms the
-// direction-1 products M1 x, J1 x, K1 x of its column from its 2P+1 neighbours
-// (neighbours in another slice are masked), keeps them in a window of 2P+1
-// rows, and emits the direction-2 outputs of the row P behind.
+// Columns are the (slice, i_1) pairs in order; a CTA owns C kAThreads
+// consecutive columns (C adjacent ones per thread: 2 in FP32, 1 in FP64) and
+// walks i_2.  Each row i_2 of the CTA's columns (plus P columns of halo on each
+// side) is staged in shared memory; every thread forms the direction-1 products
+// M1 x, J1 x, K1 x of its columns from their 2P+C neighbours (neighbours in
+// another slice are masked), keeps them in windows of 2P+1 rows, and emits the
+// direction-2 outputs of the row P behind.  Interior direction-2 band rows are
+// held in registers.
+template <typename T>
+constexpr int slice_cols() {
+  return sizeof(T) == 4 ? 2 : 1;
+}
+
 template <typename T, int P>
 __global__ void __launch_bounds__(kAThreads) slice_kernel(const __grid_constant__ SliceArgs<T> a) {
-  constexpr int W = 2 * P + 1, D = prefetch_rows<T>(), R = D + 1, RW = kAThreads + 2 * P;
+  constexpr int W = 2 * P + 1, D = prefetch_rows<T>(), R = D + 1, C = slice_cols<T>(), CC = C * kAThreads;
+  constexpr int RW = (CC + 2 * P + 3) / 4 * 4;
   __shared__ __align__(16) T ring[R][RW];
   const int tid = threadIdx.x, n1 = a.n1, n2 = a.n2, wp = a.row_stride;
   const long long area = static_cast<long long>(n1) * n2;
   const long long ncols = a.slices * n1;
-  const long long c0 = static_cast<long long>(blockIdx.x) * kAThreads;
-  const long long col = c0 + tid;
-  const bool active = col < ncols;
-  const long long s = active ? col / n1 : 0;
-  const int x = active ? static_cast<int>(col - s * n1) : 0;
-  const long long own = active ? s * area + x : 0;
+  const long long c0 = static_cast<long long>(blockIdx.x) * CC;
+  long long own[C], s[C];
+  int x[C];
+  bool act[C];
+  unsigned valid[C];  // bit w: neighbour i_1 = x - P + w lies in the slice
+  T cM[C][W], cJ[C][W], cK[C][W];
+#pragma unroll
+  for (int h = 0; h < C; ++h) {
+    const long long col = c0 + C * tid + h;
+    act[h] = col < ncols;
+    s[h] = act[h] ? col / n1 : 0;
+    x[h] = act[h] ? static_cast<int>(col - s[h] * n1) : 0;
+    own[h] = act[h] ? s[h] * area + x[h] : 0;
+    valid[h] = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w)
+      if (act[h] && x[h] - P + w >= 0 && x[h] - P + w < n1) valid[h] |= 1u << w;
+    load_row<T, W>(a.bM1 + static_cast<size_t>(x[h]) * wp, cM[h]);
+    load_row<T, W>(a.bJ1 + static_cast<size_t>(x[h]) * wp, cJ[h]);
+    load_row<T, W>(a.bK1 + static_cast<size_t>(x[h]) * wp, cK[h]);
+  }
+  // halo columns: P on each side, loaded by threads 0 .. 2P-1
   long long halo = 0;
   bool has_halo = false;
   int hslot = 0;
   if (tid < 2 * P) {
-    const long long hc = tid < P ? c0 - P + tid : c0 + kAThreads + (tid - P);
-    hslot = tid < P ? tid : kAThreads + tid;
+    const long long hc = tid < P ? c0 - P + tid : c0 + CC + (tid - P);
+    hslot = tid < P ? tid : CC + tid;
     if (hc >= 0 && hc < ncols) {
       const long long hs = hc / n1;
       halo = hs * area + (hc - hs * n1);
       has_halo = true;
     }
   }
-  unsigned valid = 0;  // bit w: neighbour i_1 = x - P + w lies in this slice
+  // interior direction-2 band rows
+  T iM2[W], iJ2[W], i2K2[W], iK2[W];
+  const int lo2 = a.lo2, hi2 = a.hi2;
+  if (lo2 < hi2) {
+    load_row<T, W>(a.bM2 + static_cast<size_t>(lo2) * wp, iM2);
+    load_row<T, W>(a.bJ2 + static_cast<size_t>(lo2) * wp, iJ2);
+    load_row<T, W>(a.b2K2 + static_cast<size_t>(lo2) * wp, i2K2);
+    load_row<T, W>(a.bK2 + static_cast<size_t>(lo2) * wp, iK2);
+  } else {
 #pragma unroll
-  for (int w = 0; w < W; ++w)
-    if (x - P + w >= 0 && x - P + w < n1) valid |= 1u << w;
-  T cM[W], cJ[W], cK[W];
-  load_row<T, W>(a.bM1 + static_cast<size_t>(x) * wp, cM);
-  load_row<T, W>(a.bJ1 + static_cast<size_t>(x) * wp, cJ);
-  load_row<T, W>(a.bK1 + static_cast<size_t>(x) * wp, cK);
+    for (int w = 0; w < W; ++w) iM2[w] = iJ2[w] = i2K2[w] = iK2[w] = T(0);
+  }
   const T *__restrict__ X = a.x;
-  // row y of this CTA's columns (and halo) into ring slot y % R, one commit group per row
   auto issue = [&](int y) {
     if (y < n2) {
       T *row = ring[y % R];
-      cp_async_elem(row + P + tid, X + own + static_cast<long long>(y) * n1, active);
+#pragma unroll
+      for (int h = 0; h < C; ++h)
+        cp_async_elem(row + P + C * tid + h, X + own[h] + static_cast<long long>(y) * n1, act[h]);
       if (tid < 2 * P) cp_async_elem(row + hslot, X + halo + static_cast<long long>(y) * n1, has_halo);
     }
     cp_async_commit();
   };
 #pragma unroll
   for (int e = 0; e < D; ++e) issue(e);
-  T wm[W], wj[W], wk[W];
+  T wm[C][W], wj[C][W], wk[C][W];
 #pragma unroll
-  for (int w = 0; w < W; ++w) wm[w] = wj[w] = wk[w] = T(0);
-  const bool ls_row = a.ls_last != nullptr && active && (s % a.n_t) == a.n_t - 1;
+  for (int h = 0; h < C; ++h)
+#pragma unroll
+    for (int w = 0; w < W; ++w) wm[h][w] = wj[h][w] = wk[h][w] = T(0);
+  bool ls_row[C], need_k = a.ls_last == nullptr;
+#pragma unroll
+  for (int h = 0; h < C; ++h) {
+    ls_row[h] = a.ls_last != nullptr && act[h] && (s[h] % a.n_t) == a.n_t - 1;
+    need_k = need_k || ls_row[h];
+  }
   for (int yy = 0; yy < n2 + P; ++yy) {
-    // Row yy has landed once at most D - 1 younger groups are pending; the
-    // barrier publishes every thread's copies.  Slot (yy + D) % R, refilled
-    // below, was last read at row yy - 1, before this barrier.
     cp_async_wait<D - 1>();
     __syncthreads();
-    T m0 = T(0), j0 = T(0), k0 = T(0);
-    if (yy < n2) {
-      const T *row = ring[yy % R];
-      T v[W];
+    T m0[C], j0[C], k0[C];
 #pragma unroll
-      for (int w = 0; w < W; ++w) v[w] = ((valid >> w) & 1u) ? row[tid + w] : T(0);
-      m0 = band_dot(cM, v, T(0));
-      j0 = band_dot(cJ, v, T(0));
-      k0 = band_dot(cK, v, T(0));
+    for (int h = 0; h < C; ++h) m0[h] = j0[h] = k0[h] = T(0);
+    if (yy < n2) {
+      const T *row = ring[yy % R] + C * tid;
+      T v[W + C - 1];
+#pragma unroll
+      for (int w = 0; w < W + C - 1; ++w) v[w] = row[w];
+#pragma unroll
+      for (int h = 0; h < C; ++h) {
+        T u[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) u[w] = ((valid[h] >> w) & 1u) ? v[w + h] : T(0);
+        m0[h] = band_dot(cM[h], u, T(0));
+        j0[h] = band_dot(cJ[h], u, T(0));
+        k0[h] = band_dot(cK[h], u, T(0));
+      }
     }
     issue(yy + D);
-    slide(wm, m0);
-    slide(wj, j0);
-    slide(wk, k0);
+#pragma unroll
+    for (int h = 0; h < C; ++h) {
+      slide(wm[h], m0[h]);
+      slide(wj[h], j0[h]);
+      slide(wk[h], k0[h]);
+    }
     const int y = yy - P;
-    if (y >= 0 && active) {
-      const size_t r = static_cast<size_t>(y) * wp;
-      T c[W];
-      load_row<T, W>(a.bM2 + r, c);
-      const T om = band_dot(c, wm, T(0));
-      T oj = band_dot(c, wj, T(0));
-      T ok = T(0);
-      if (a.ls_last == nullptr || ls_row) ok = band_dot(c, wk, T(0));
-      load_row<T, W>(a.bJ2 + r, c);
-      oj = band_dot(c, wm, oj);
-      load_row<T, W>(a.b2K2 + r, c);
-      oj = band_dot(c, wk, oj);
-      const long long off = own + static_cast<long long>(y) * n1;
-      a.out_m[off] = om;
-      a.out_j[off] = oj;
-      if (a.ls_last == nullptr || ls_row) {
-        load_row<T, W>(a.bK2 + r, c);
-        ok = band_dot(c, wm, ok);
-        if (a.ls_last == nullptr)
-          a.out_k[off] = ok;
-        else
-          a.ls_last[(s / a.n_t) * area + static_cast<long long>(y) * n1 + x] = ok;
+    if (y >= 0) {
+      T c2M[W], c2J[W], c22K[W], c2K[W];
+      band_row<T, W>(a.bM2, y, wp, lo2, hi2, iM2, c2M);
+      band_row<T, W>(a.bJ2, y, wp, lo2, hi2, iJ2, c2J);
+      band_row<T, W>(a.b2K2, y, wp, lo2, hi2, i2K2, c22K);
+      if (need_k) band_row<T, W>(a.bK2, y, wp, lo2, hi2, iK2, c2K);
+#pragma unroll
+      for (int h = 0; h < C; ++h) {
+        if (!act[h]) continue;
+        const T om = band_dot(c2M, wm[h], T(0));
+        T oj = band_dot(c2M, wj[h], T(0));
+        oj = band_dot(c2J, wm[h], oj);
+        oj = band_dot(c22K, wk[h], oj);
+        const long long off = own[h] + static_cast<long long>(y) * n1;
+        a.out_m[off] = om;
+        a.out_j[off] = oj;
+        if (a.ls_last == nullptr || ls_row[h]) {
+          T ok = band_dot(c2M, wk[h], T(0));
+          ok = band_dot(c2K, wm[h], ok);
+          if (a.ls_last == nullptr)
+            a.out_k[off] = ok;
+          else
+            a.ls_last[(s[h] / a.n_t) * area + static_cast<long long>(y) * n1 + x[h]] = ok;
+        }
       }
     }
   }
@@ -203,125 +264,136 @@ __global__ void __launch_bounds__(kAThreads) slice_kernel(const __grid_constant_
 }
 
 // ---- direction 3 ------------------------------------------------------------------------
-// One thread per (b, t, i_1, i_2) column, walking i_3 with a register window
-// for each of m, j', k and a ring of D rows already in flight.
+// One thread per (b, t, i_1, i_2) column, walking i_3 with a register window of
+// 2P+1 rows for each of m, j', k, fed by a register queue of the next 2P+1 rows
+// (loads issued 2P+1 rows ahead; the loop is unrolled so that every queue slot
+// is a fixed register).  Interior band rows are held in registers.
 template <typename T, int P>
 __global__ void __launch_bounds__(kAThreads) zpass_kernel(const __grid_constant__ ZArgs<T> a) {
-  constexpr int W = 2 * P + 1, D = prefetch_rows<T>();
-  // thread-private rings: ring[slot][input][thread]
-  __shared__ __align__(16) T ring[D][3][kAThreads];
+  constexpr int W = 2 * P + 1;
   const int tid = threadIdx.x;
   const long long col = static_cast<long long>(blockIdx.x) * kAThreads + tid;
   if (col >= a.outer * a.inner) return;  // no block-wide barrier below
   const long long inner = a.inner, o = col / inner, cc = col - o * inner;
-  const int n = a.n, wp = a.row_stride;
+  const int n = a.n, wp = a.row_stride, lo = a.lo, hi = a.hi;
   const long long base = o * n * inner + cc;
   const T *__restrict__ Im = a.m + base;
   const T *__restrict__ Ij = a.j + base;
   const T *__restrict__ Ik = a.k + base;
   auto ld = [&](const T *__restrict__ p, int r) -> T { return (r >= 0 && r < n) ? p[r * inner] : T(0); };
-  // row r (>= P + 1) into slot r % D, one commit group per row
-  auto issue = [&](int r) {
-    const bool ok = r < n;
-    const long long off = ok ? static_cast<long long>(r) * inner : 0;
-    cp_async_elem(&ring[r % D][0][tid], Im + off, ok);
-    cp_async_elem(&ring[r % D][1][tid], Ij + off, ok);
-    cp_async_elem(&ring[r % D][2][tid], Ik + off, ok);
-    cp_async_commit();
-  };
+  T iM[W], iJ[W], i2K[W], iK[W];
+  if (lo < hi) {
+    load_row<T, W>(a.bM + static_cast<size_t>(lo) * wp, iM);
+    load_row<T, W>(a.bJ + static_cast<size_t>(lo) * wp, iJ);
+    load_row<T, W>(a.b2K + static_cast<size_t>(lo) * wp, i2K);
+    load_row<T, W>(a.bK + static_cast<size_t>(lo) * wp, iK);
+  } else {
 #pragma unroll
-  for (int e = 0; e < D; ++e) issue(P + 1 + e);
-  T wm[W], wj[W], wk[W];
+    for (int w = 0; w < W; ++w) iM[w] = iJ[w] = i2K[w] = iK[w] = T(0);
+  }
+  T wm[W], wj[W], wk[W], qm[W], qj[W], qk[W];
 #pragma unroll
   for (int w = 0; w < W; ++w) {
     wm[w] = ld(Im, w - P);
     wj[w] = ld(Ij, w - P);
     wk[w] = ld(Ik, w - P);
+    qm[w] = ld(Im, P + 1 + w);
+    qj[w] = ld(Ij, P + 1 + w);
+    qk[w] = ld(Ik, P + 1 + w);
   }
   const bool ls_col = a.ls_last != nullptr && (o % a.n_t) == a.n_t - 1;
   T *ls = ls_col ? a.ls_last + (o / a.n_t) * n * inner + cc : nullptr;
-  for (int i = 0; i < n; ++i) {
-    const size_t r = static_cast<size_t>(i) * wp;
-    T c[W];
-    load_row<T, W>(a.bM + r, c);
-    const T oms = band_dot(c, wm, T(0));
-    T ojs = band_dot(c, wj, T(0));
-    T ols = T(0);
-    if (ls_col) ols = band_dot(c, wk, T(0));
-    load_row<T, W>(a.bJ + r, c);
-    ojs = band_dot(c, wm, ojs);
-    load_row<T, W>(a.b2K + r, c);
-    ojs = band_dot(c, wk, ojs);
-    a.Ms[base + static_cast<long long>(i) * inner] = oms;
-    a.Js[base + static_cast<long long>(i) * inner] = ojs;
-    if (ls_col) {
-      load_row<T, W>(a.bK + r, c);
-      ls[static_cast<long long>(i) * inner] = band_dot(c, wm, ols);
+  for (int i0 = 0; i0 < n; i0 += W) {
+#pragma unroll
+    for (int u = 0; u < W; ++u) {
+      const int i = i0 + u;
+      if (i < n) {
+        T cM[W], cJ[W], c2K[W];
+        band_row<T, W>(a.bM, i, wp, lo, hi, iM, cM);
+        band_row<T, W>(a.bJ, i, wp, lo, hi, iJ, cJ);
+        band_row<T, W>(a.b2K, i, wp, lo, hi, i2K, c2K);
+        const T oms = band_dot(cM, wm, T(0));
+        T ojs = band_dot(cM, wj, T(0));
+        ojs = band_dot(cJ, wm, ojs);
+        ojs = band_dot(c2K, wk, ojs);
+        a.Ms[base + static_cast<long long>(i) * inner] = oms;
+        a.Js[base + static_cast<long long>(i) * inner] = ojs;
+        if (ls_col) {
+          T cK[W];
+          band_row<T, W>(a.bK, i, wp, lo, hi, iK, cK);
+          T ols = band_dot(cM, wk, T(0));
+          ls[static_cast<long long>(i) * inner] = band_dot(cK, wm, ols);
+        }
+      }
+      // the window takes row i + P + 1 from queue slot u, which then loads row i + P + 1 + W
+      slide(wm, qm[u]);
+      slide(wj, qj[u]);
+      slide(wk, qk[u]);
+      qm[u] = ld(Im, i + P + 1 + W);
+      qj[u] = ld(Ij, i + P + 1 + W);
+      qk[u] = ld(Ik, i + P + 1 + W);
     }
-    // the window takes row i + P + 1 (its group is the oldest of the D pending)
-    cp_async_wait<D - 1>();
-    const int nr = i + P + 1, sl = nr % D;
-    slide(wm, ring[sl][0][tid]);
-    slide(wj, ring[sl][1][tid]);
-    slide(wk, ring[sl][2][tid]);
-    issue(nr + D);
   }
-  cp_async_wait<0>();
 }
 
 // ---- time direction -------------------------------------------------------------------
-// y = K_t (x) (M_s x) + M_t (x) (J_s x), and + L_s x on the last time slice.
+// y = K_t (x) (M_s x) + M_t (x) (J_s x), and + L_s x on the last time slice;
+// same register window and queue as the direction-3 pass.
 template <typename T, int P>
 __global__ void __launch_bounds__(kAThreads) tpass_kernel(const __grid_constant__ TArgs<T> a) {
-  constexpr int W = 2 * P + 1, D = prefetch_rows<T>();
-  __shared__ __align__(16) T ring[D][2][kAThreads];
+  constexpr int W = 2 * P + 1;
   const int tid = threadIdx.x;
   const long long col = static_cast<long long>(blockIdx.x) * kAThreads + tid;
   if (col >= a.outer * a.inner) return;  // no block-wide barrier below
   const long long inner = a.inner, o = col / inner, cc = col - o * inner;
-  const int n = a.n, wp = a.row_stride;
+  const int n = a.n, wp = a.row_stride, lo = a.lo, hi = a.hi;
   const long long base = o * n * inner + cc;
   const T *__restrict__ Ims = a.Ms + base;
   const T *__restrict__ Ijs = a.Js + base;
   auto ld = [&](const T *__restrict__ p, int r) -> T { return (r >= 0 && r < n) ? p[r * inner] : T(0); };
-  auto issue = [&](int r) {
-    const bool ok = r < n;
-    const long long off = ok ? static_cast<long long>(r) * inner : 0;
-    cp_async_elem(&ring[r % D][0][tid], Ims + off, ok);
-    cp_async_elem(&ring[r % D][1][tid], Ijs + off, ok);
-    cp_async_commit();
-  };
+  T iK[W], iM[W];
+  if (lo < hi) {
+    load_row<T, W>(a.bK + static_cast<size_t>(lo) * wp, iK);
+    load_row<T, W>(a.bM + static_cast<size_t>(lo) * wp, iM);
+  } else {
 #pragma unroll
-  for (int e = 0; e < D; ++e) issue(P + 1 + e);
-  T wm[W], wj[W];
+    for (int w = 0; w < W; ++w) iK[w] = iM[w] = T(0);
+  }
+  T wm[W], wj[W], qm[W], qj[W];
 #pragma unroll
   for (int w = 0; w < W; ++w) {
     wm[w] = ld(Ims, w - P);
     wj[w] = ld(Ijs, w - P);
+    qm[w] = ld(Ims, P + 1 + w);
+    qj[w] = ld(Ijs, P + 1 + w);
   }
-  for (int i = 0; i < n; ++i) {
-    const size_t r = static_cast<size_t>(i) * wp;
-    T c[W];
-    load_row<T, W>(a.bK + r, c);
-    T out = band_dot(c, wm, T(0));
-    load_row<T, W>(a.bM + r, c);
-    out = band_dot(c, wj, out);
-    if (i == n - 1) out += a.ls_last[o * inner + cc];
-    a.y[base + static_cast<long long>(i) * inner] = out;
-    cp_async_wait<D - 1>();
-    const int nr = i + P + 1, sl = nr % D;
-    slide(wm, ring[sl][0][tid]);
-    slide(wj, ring[sl][1][tid]);
-    issue(nr + D);
+  for (int i0 = 0; i0 < n; i0 += W) {
+#pragma unroll
+    for (int u = 0; u < W; ++u) {
+      const int i = i0 + u;
+      if (i < n) {
+        T cK[W], cM[W];
+        band_row<T, W>(a.bK, i, wp, lo, hi, iK, cK);
+        band_row<T, W>(a.bM, i, wp, lo, hi, iM, cM);
+        T out = band_dot(cK, wm, T(0));
+        out = band_dot(cM, wj, out);
+        if (i == n - 1) out += a.ls_last[o * inner + cc];
+        a.y[base + static_cast<long long>(i) * inner] = out;
+      }
+      slide(wm, qm[u]);
+      slide(wj, qj[u]);
+      qm[u] = ld(Ims, i + P + 1 + W);
+      qj[u] = ld(Ijs, i + P + 1 + W);
+    }
   }
-  cp_async_wait<0>();
 }
 
 long long blocks_for(long long cols) { return (cols + kAThreads - 1) / kAThreads; }
 
 template <typename T, int P>
 cudaError_t launch_slice_p(const SliceArgs<T> &a, cudaStream_t s) {
-  const long long g = blocks_for(a.slices * a.n1);
+  constexpr long long cc = slice_cols<T>() * kAThreads;
+  const long long g = (a.slices * a.n1 + cc - 1) / cc;
   if (g > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
   if (g > 0) slice_kernel<T, P><<<static_cast<unsigned>(g), kAThreads, 0, s>>>(a);
   return cudaGetLastError();
@@ -409,6 +481,8 @@ cudaError_t launch_fused_A(const FusedA<T> &f, const T *x, T *y, cudaStream_t s)
   sa.n2 = f.n[1];
   sa.n_t = f.n_t;
   sa.row_stride = ws;
+  sa.lo2 = f.lo[1];
+  sa.hi2 = f.hi[1];
   T *Ms = f.work[3], *Js = f.work[4];
   if (f.d == 3) {
     sa.out_m = f.work[0];
@@ -441,6 +515,8 @@ cudaError_t launch_fused_A(const FusedA<T> &f, const T *x, T *y, cudaStream_t s)
     za.n = f.n[2];
     za.n_t = f.n_t;
     za.row_stride = ws;
+    za.lo = f.lo[2];
+    za.hi = f.hi[2];
     e = dispatch_zpass<T>(f.p_s, za, s);
     if (e != cudaSuccess) return e;
   }
@@ -456,8 +532,29 @@ cudaError_t launch_fused_A(const FusedA<T> &f, const T *x, T *y, cudaStream_t s)
   ta.inner = Ns;
   ta.n = f.n_t;
   ta.row_stride = wt;
+  ta.lo = f.lo_t;
+  ta.hi = f.hi_t;
   return dispatch_tpass<T>(f.p_t, ta, s);
 }
+
+template <typename T>
+void toeplitz_rows(const T *const *bands, int nbands, int n, int stride, int *lo, int *hi) {
+  const int mid = n / 2;
+  auto same = [&](int i) {
+    for (int b = 0; b < nbands; ++b)
+      if (std::memcmp(bands[b] + static_cast<size_t>(i) * stride, bands[b] + static_cast<size_t>(mid) * stride,
+                      sizeof(T) * stride) != 0)
+        return false;
+    return true;
+  };
+  int l = mid, h = mid + 1;
+  while (l > 0 && same(l - 1)) --l;
+  while (h < n && same(h)) ++h;
+  *lo = n > 0 ? l : 0;
+  *hi = n > 0 ? h : 0;
+}
+template void toeplitz_rows<double>(const double *const *, int, int, int, int *, int *);
+template void toeplitz_rows<float>(const float *const *, int, int, int, int *, int *);
 
 template cudaError_t launch_fused_A<double>(const FusedA<double> &, const double *, double *, cudaStream_t);
 template cudaError_t launch_fused_A<float>(const FusedA<float> &, const float *, float *, cudaStream_t);

@@ -34,6 +34,7 @@ struct SliceArgs {
   const T *bM1, *bJ1, *bK1, *bM2, *bJ2, *bK2, *b2K2;
   long long slices;  // number of n2 x n1 slices
   int n1, n2, n_t, row_stride;
+  int lo2, hi2;      // rows [lo2, hi2) of the direction-2 bands are all equal (uniform knots)
 };
 template <typename T>
 struct ZArgs {
@@ -42,6 +43,7 @@ struct ZArgs {
   const T *bM, *bJ, *bK, *b2K;
   long long outer, inner;  // outer = B n_t, inner = n1 n2
   int n, n_t, row_stride;
+  int lo, hi;              // rows [lo, hi) of the bands are all equal
 };
 template <typename T>
 struct TArgs {
@@ -50,6 +52,7 @@ struct TArgs {
   const T *bK, *bM;
   long long outer, inner;  // outer = B, inner = N_s
   int n, row_stride;
+  int lo, hi;              // rows [lo, hi) of the bands are all equal
 };
 template <typename T>
 struct FusedA {
@@ -58,7 +61,15 @@ struct FusedA {
   const T *bKt, *bMt;                       // padded time bands
   T *work[5];                               // d = 3: m, j', k, M_s x, J_s x; d = 2: work[3..4]
   T *ls_last;                               // B * N_s
+  // rows [lo, hi) of every band of a direction are identical (the interior
+  // rows of uniform-knot Galerkin matrices); lo = hi = 0 when none are
+  int lo[3], hi[3], lo_t, hi_t;
 };
+// Largest run of rows around the middle row of an n x stride band array in
+// which every one of the given arrays has rows identical (bitwise) to its
+// middle row; writes [lo, hi).
+template <typename T>
+void toeplitz_rows(const T *const *bands, int nbands, int n, int stride, int *lo, int *hi);
 // y = A x; 2 launches (d = 2) or 3 (d = 3).  x, y: B * N values, colexicographic.
 template <typename T>
 cudaError_t launch_fused_A(const FusedA<T> &f, const T *x, T *y, cudaStream_t s);

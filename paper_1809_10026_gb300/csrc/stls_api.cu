@@ -31,6 +31,7 @@ struct AOps {
   // the same bands with rows padded to whole 16-byte vectors, and 2 K (fused A x)
   T *pad_M[3] = {}, *pad_K[3] = {}, *pad_J[3] = {}, *pad_2K[3] = {};
   T *pad_Kt = nullptr, *pad_Mt = nullptr;
+  int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0}, lo_t = 0, hi_t = 0;  // identical interior band rows
   T *abuf[8] = {};
   T *ls_buf = nullptr;
 };
@@ -126,10 +127,26 @@ template <typename T>
 int upload_padded(stls_ctx *c, AOps<T> &A, int k, const stls::Dir1D &D, const std::vector<double> &bM,
                   const std::vector<double> &bK, const std::vector<double> &bJ) {
   const int st = stls::band_row_stride(D.p, sizeof(T));
-  int rc = upload(c, &A.pad_M[k], pad_band<T>(bM, D.n, D.p, st, 1.0));
-  if (!rc) rc = upload(c, &A.pad_K[k], pad_band<T>(bK, D.n, D.p, st, 1.0));
-  if (!rc) rc = upload(c, &A.pad_J[k], pad_band<T>(bJ, D.n, D.p, st, 1.0));
-  if (!rc) rc = upload(c, &A.pad_2K[k], pad_band<T>(bK, D.n, D.p, st, 2.0));
+  const std::vector<T> pM = pad_band<T>(bM, D.n, D.p, st, 1.0), pK = pad_band<T>(bK, D.n, D.p, st, 1.0);
+  const std::vector<T> pJ = pad_band<T>(bJ, D.n, D.p, st, 1.0), p2K = pad_band<T>(bK, D.n, D.p, st, 2.0);
+  const T *all[4] = {pM.data(), pK.data(), pJ.data(), p2K.data()};
+  stls::toeplitz_rows<T>(all, 4, D.n, st, &A.lo[k], &A.hi[k]);
+  int rc = upload(c, &A.pad_M[k], pM);
+  if (!rc) rc = upload(c, &A.pad_K[k], pK);
+  if (!rc) rc = upload(c, &A.pad_J[k], pJ);
+  if (!rc) rc = upload(c, &A.pad_2K[k], p2K);
+  return rc;
+}
+
+template <typename T>
+int upload_padded_time(stls_ctx *c, AOps<T> &A, const stls::Dir1D &Tm, const std::vector<double> &bKt,
+                       const std::vector<double> &bMt) {
+  const int st = stls::band_row_stride(Tm.p, sizeof(T));
+  const std::vector<T> pK = pad_band<T>(bKt, Tm.n, Tm.p, st, 1.0), pM = pad_band<T>(bMt, Tm.n, Tm.p, st, 1.0);
+  const T *all[2] = {pK.data(), pM.data()};
+  stls::toeplitz_rows<T>(all, 2, Tm.n, st, &A.lo_t, &A.hi_t);
+  int rc = upload(c, &A.pad_Kt, pK);
+  if (!rc) rc = upload(c, &A.pad_Mt, pM);
   return rc;
 }
 
@@ -297,6 +314,12 @@ int apply_A_impl(stls_ctx *c, AOps<T> &A, const T *x, T *y) {
     f.B = c->B;
     f.bKt = A.pad_Kt;
     f.bMt = A.pad_Mt;
+    for (int k = 0; k < 3; ++k) {
+      f.lo[k] = A.lo[k];
+      f.hi[k] = A.hi[k];
+    }
+    f.lo_t = A.lo_t;
+    f.hi_t = A.hi_t;
     for (int w = 0; w < 5; ++w) f.work[w] = A.abuf[w];
     f.ls_last = A.ls_buf;
     c->launches += c->d - 1;  // d launches in all
@@ -654,11 +677,8 @@ int stls_create(stls_ctx **out, const stls_params *prm, void *cuda_stream) {
     if (!rc) rc = upload(c, &c->a64.band_Mt, bMt);
     if (!rc && refine) rc = upload(c, &c->a32.band_Kt, to_f32(bKt));
     if (!rc && refine) rc = upload(c, &c->a32.band_Mt, to_f32(bMt));
-    const int st64 = stls::band_row_stride(Tm.p, 8), st32 = stls::band_row_stride(Tm.p, 4);
-    if (!rc) rc = upload(c, &c->a64.pad_Kt, pad_band<double>(bKt, Tm.n, Tm.p, st64, 1.0));
-    if (!rc) rc = upload(c, &c->a64.pad_Mt, pad_band<double>(bMt, Tm.n, Tm.p, st64, 1.0));
-    if (!rc && refine) rc = upload(c, &c->a32.pad_Kt, pad_band<float>(bKt, Tm.n, Tm.p, st32, 1.0));
-    if (!rc && refine) rc = upload(c, &c->a32.pad_Mt, pad_band<float>(bMt, Tm.n, Tm.p, st32, 1.0));
+    if (!rc) rc = upload_padded_time(c, c->a64, Tm, bKt, bMt);
+    if (!rc && refine) rc = upload_padded_time(c, c->a32, Tm, bKt, bMt);
   }
   if (!rc) rc = upload(c, &c->Uf[c->d], transpose(c->hs.eig_t.U, Tm.n));
   if (!rc) rc = upload(c, &c->Ub[c->d], c->hs.eig_t.U);
