@@ -204,7 +204,9 @@ __global__ void __launch_bounds__(kAThreads) slice_kernel(const __grid_constant_
     ls_row[h] = a.ls_last != nullptr && act[h] && (s[h] % a.n_t) == a.n_t - 1;
     need_k = need_k || ls_row[h];
   }
-  for (int yy = 0; yy < n2 + P; ++yy) {
+  // one row yy: direction 1 of row yy (from the staged row), then direction 2
+  // of row y = yy - P with band rows c2M, c2J, c22K, c2K
+  auto row_step = [&](int yy, const T(&c2M)[W], const T(&c2J)[W], const T(&c22K)[W], const T(&c2K)[W]) {
     cp_async_wait<D - 1>();
     __syncthreads();
     T m0[C], j0[C], k0[C];
@@ -234,11 +236,6 @@ __global__ void __launch_bounds__(kAThreads) slice_kernel(const __grid_constant_
     }
     const int y = yy - P;
     if (y >= 0) {
-      T c2M[W], c2J[W], c22K[W], c2K[W];
-      band_row<T, W>(a.bM2, y, wp, lo2, hi2, iM2, c2M);
-      band_row<T, W>(a.bJ2, y, wp, lo2, hi2, iJ2, c2J);
-      band_row<T, W>(a.b2K2, y, wp, lo2, hi2, i2K2, c22K);
-      if (need_k) band_row<T, W>(a.bK2, y, wp, lo2, hi2, iK2, c2K);
 #pragma unroll
       for (int h = 0; h < C; ++h) {
         if (!act[h]) continue;
@@ -257,6 +254,26 @@ __global__ void __launch_bounds__(kAThreads) slice_kernel(const __grid_constant_
           else
             a.ls_last[(s[h] / a.n_t) * area + static_cast<long long>(y) * n1 + x[h]] = ok;
         }
+      }
+    }
+  };
+  for (int yy0 = 0; yy0 < n2 + P; yy0 += W) {
+    if (yy0 - P >= lo2 && yy0 - P + W <= hi2) {
+      // a whole group of interior direction-2 rows: the band rows are the registers
+#pragma unroll
+      for (int u = 0; u < W; ++u) row_step(yy0 + u, iM2, iJ2, i2K2, iK2);
+    } else {
+#pragma unroll 1
+      for (int u = 0; u < W && yy0 + u < n2 + P; ++u) {
+        const int y = yy0 + u - P;
+        T c2M[W], c2J[W], c22K[W], c2K[W];
+        if (y >= 0) {
+          band_row<T, W>(a.bM2, y, wp, lo2, hi2, iM2, c2M);
+          band_row<T, W>(a.bJ2, y, wp, lo2, hi2, iJ2, c2J);
+          band_row<T, W>(a.b2K2, y, wp, lo2, hi2, i2K2, c22K);
+          if (need_k) band_row<T, W>(a.bK2, y, wp, lo2, hi2, iK2, c2K);
+        }
+        row_step(yy0 + u, c2M, c2J, c22K, c2K);
       }
     }
   }
@@ -303,35 +320,47 @@ __global__ void __launch_bounds__(kAThreads) zpass_kernel(const __grid_constant_
   }
   const bool ls_col = a.ls_last != nullptr && (o % a.n_t) == a.n_t - 1;
   T *ls = ls_col ? a.ls_last + (o / a.n_t) * n * inner + cc : nullptr;
+  // outputs of row i from the window, with band rows cM, cJ, c2K, cK
+  auto emit = [&](int i, const T(&cM)[W], const T(&cJ)[W], const T(&c2K)[W], const T(&cK)[W]) {
+    const T oms = band_dot(cM, wm, T(0));
+    T ojs = band_dot(cM, wj, T(0));
+    ojs = band_dot(cJ, wm, ojs);
+    ojs = band_dot(c2K, wk, ojs);
+    a.Ms[base + static_cast<long long>(i) * inner] = oms;
+    a.Js[base + static_cast<long long>(i) * inner] = ojs;
+    if (ls_col) ls[static_cast<long long>(i) * inner] = band_dot(cK, wm, band_dot(cM, wk, T(0)));
+  };
+  // the window takes row i + P + 1 from queue slot u, which then loads row i + P + 1 + W
+  auto advance = [&](int i, int u) {
+    slide(wm, qm[u]);
+    slide(wj, qj[u]);
+    slide(wk, qk[u]);
+    qm[u] = ld(Im, i + P + 1 + W);
+    qj[u] = ld(Ij, i + P + 1 + W);
+    qk[u] = ld(Ik, i + P + 1 + W);
+  };
   for (int i0 = 0; i0 < n; i0 += W) {
+    if (i0 >= lo && i0 + W <= hi) {
+      // a whole group of interior rows: the band rows are the registers
 #pragma unroll
-    for (int u = 0; u < W; ++u) {
-      const int i = i0 + u;
-      if (i < n) {
-        T cM[W], cJ[W], c2K[W];
-        band_row<T, W>(a.bM, i, wp, lo, hi, iM, cM);
-        band_row<T, W>(a.bJ, i, wp, lo, hi, iJ, cJ);
-        band_row<T, W>(a.b2K, i, wp, lo, hi, i2K, c2K);
-        const T oms = band_dot(cM, wm, T(0));
-        T ojs = band_dot(cM, wj, T(0));
-        ojs = band_dot(cJ, wm, ojs);
-        ojs = band_dot(c2K, wk, ojs);
-        a.Ms[base + static_cast<long long>(i) * inner] = oms;
-        a.Js[base + static_cast<long long>(i) * inner] = ojs;
-        if (ls_col) {
-          T cK[W];
-          band_row<T, W>(a.bK, i, wp, lo, hi, iK, cK);
-          T ols = band_dot(cM, wk, T(0));
-          ls[static_cast<long long>(i) * inner] = band_dot(cK, wm, ols);
-        }
+      for (int u = 0; u < W; ++u) {
+        emit(i0 + u, iM, iJ, i2K, iK);
+        advance(i0 + u, u);
       }
-      // the window takes row i + P + 1 from queue slot u, which then loads row i + P + 1 + W
-      slide(wm, qm[u]);
-      slide(wj, qj[u]);
-      slide(wk, qk[u]);
-      qm[u] = ld(Im, i + P + 1 + W);
-      qj[u] = ld(Ij, i + P + 1 + W);
-      qk[u] = ld(Ik, i + P + 1 + W);
+    } else {
+#pragma unroll
+      for (int u = 0; u < W; ++u) {
+        const int i = i0 + u;
+        if (i < n) {
+          T cM[W], cJ[W], c2K[W], cK[W];
+          band_row<T, W>(a.bM, i, wp, lo, hi, iM, cM);
+          band_row<T, W>(a.bJ, i, wp, lo, hi, iJ, cJ);
+          band_row<T, W>(a.b2K, i, wp, lo, hi, i2K, c2K);
+          if (ls_col) band_row<T, W>(a.bK, i, wp, lo, hi, iK, cK);
+          emit(i, cM, cJ, c2K, cK);
+        }
+        advance(i, u);
+      }
     }
   }
 }
@@ -367,23 +396,37 @@ __global__ void __launch_bounds__(kAThreads) tpass_kernel(const __grid_constant_
     qm[w] = ld(Ims, P + 1 + w);
     qj[w] = ld(Ijs, P + 1 + w);
   }
+  auto emit = [&](int i, const T(&cK)[W], const T(&cM)[W]) {
+    T out = band_dot(cK, wm, T(0));
+    out = band_dot(cM, wj, out);
+    if (i == n - 1) out += a.ls_last[o * inner + cc];
+    a.y[base + static_cast<long long>(i) * inner] = out;
+  };
+  auto advance = [&](int i, int u) {
+    slide(wm, qm[u]);
+    slide(wj, qj[u]);
+    qm[u] = ld(Ims, i + P + 1 + W);
+    qj[u] = ld(Ijs, i + P + 1 + W);
+  };
   for (int i0 = 0; i0 < n; i0 += W) {
+    if (i0 >= lo && i0 + W <= hi) {
 #pragma unroll
-    for (int u = 0; u < W; ++u) {
-      const int i = i0 + u;
-      if (i < n) {
-        T cK[W], cM[W];
-        band_row<T, W>(a.bK, i, wp, lo, hi, iK, cK);
-        band_row<T, W>(a.bM, i, wp, lo, hi, iM, cM);
-        T out = band_dot(cK, wm, T(0));
-        out = band_dot(cM, wj, out);
-        if (i == n - 1) out += a.ls_last[o * inner + cc];
-        a.y[base + static_cast<long long>(i) * inner] = out;
+      for (int u = 0; u < W; ++u) {
+        emit(i0 + u, iK, iM);
+        advance(i0 + u, u);
       }
-      slide(wm, qm[u]);
-      slide(wj, qj[u]);
-      qm[u] = ld(Ims, i + P + 1 + W);
-      qj[u] = ld(Ijs, i + P + 1 + W);
+    } else {
+#pragma unroll
+      for (int u = 0; u < W; ++u) {
+        const int i = i0 + u;
+        if (i < n) {
+          T cK[W], cM[W];
+          band_row<T, W>(a.bK, i, wp, lo, hi, iK, cK);
+          band_row<T, W>(a.bM, i, wp, lo, hi, iM, cM);
+          emit(i, cK, cM);
+        }
+        advance(i, u);
+      }
     }
   }
 }

@@ -56,7 +56,8 @@ namespace {
 using bf16 = __nv_bfloat16;
 
 constexpr int kThreads = 128;
-constexpr int kSlabThreads = 384;      // two consumer warpgroups and one producer warpgroup
+constexpr int kSlabGroups = 3;         // independent warpgroup chains per slab CTA
+constexpr int kSlabThreads = 128 * kSlabGroups;
 constexpr int kSlabMaxN = 256;         // columns of the slab kernel's first product (MMA N)
 constexpr int kTileN = 128;            // columns per streaming tile (MMA N)
 constexpr int kAtomCols = 64;          // BF16 columns per 128-byte swizzle atom
@@ -139,20 +140,21 @@ struct SlabArgs {
   uint32_t lbo_b1;      // K-chunk stride of the data operand: G * Rb * 16
   int off_A, off_B2, off_B1, off_A2, off_raw, off_out;  // buffers 0 and 1 follow each other
   int szA, szB2, szB1, szA2, szRaw, szOut;
-  uint32_t idesc1, idesc2, tmem_cols;               // tmem_cols per accumulator buffer
+  uint32_t idesc1, idesc2, tmem_cols, tmem_alloc;   // tmem_cols per group, tmem_alloc in all
+  int groups;                                       // warpgroups with a chain (2 or 3)
   int *err;
 };
 
-// Warp roles: warpgroup 2 (producer) waits for the bulk copy of a step's input,
-// converts it to the BF16 data operand and issues product 1; warpgroups 0 and
-// 1 (consumers) take the even and odd steps: epilogue 1, product 2, epilogue 2
-// and the output store.  Steps alternate between two sets of buffers (input,
-// data operand, product-2 A operand, staging, accumulator columns), so the
-// producer converts step i+1 while a consumer finishes step i.
+// Warpgroups: the CTA's steps i = 0, 1, ... are dealt round-robin to its
+// kSlabGroups (or 2, when the buffers of three do not fit) warpgroups; each runs
+// the whole chain of its steps (input copy, conversion, product 1, epilogue 1,
+// product 2, epilogue 2, output store) with its own buffers, tensor-memory
+// columns, mbarriers and named barrier, so the chains of the groups overlap.
+// Only the two eigenvector images are shared.
 template <typename InT, typename OutT>
 __global__ void __launch_bounds__(kSlabThreads, 1) slab_kernel(SlabArgs a) {
   extern __shared__ uint8_t smem_dyn[];
-  __shared__ __align__(8) uint64_t bar_raw[2], bar_mma1[2], bar_mma2[2], bar_dfree[2], bar_fin[3];
+  __shared__ __align__(8) uint64_t bar_raw[kSlabGroups], bar_mma[kSlabGroups];
   __shared__ uint32_t tmem_holder;
   __shared__ int abort_flag;
   __shared__ uint16_t row_n[kSlabMaxN];  // data-operand row of input row g * nb + b
@@ -160,6 +162,7 @@ __global__ void __launch_bounds__(kSlabThreads, 1) slab_kernel(SlabArgs a) {
   const uint8_t *sA = sm + a.off_A, *sB2 = sm + a.off_B2;
   const int tid = threadIdx.x, warp = tid >> 5, wg = warp >> 2;
   const int lt = tid & 127;  // thread index within the warpgroup
+  const int ngroups = a.groups;
   const long long nsteps = (a.nsl + a.G - 1) / a.G;
   const long long nloc = blockIdx.x < nsteps ? (nsteps - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const long long slice_in = static_cast<long long>(a.nb) * a.in_pitch * sizeof(InT);     // bytes
@@ -167,17 +170,14 @@ __global__ void __launch_bounds__(kSlabThreads, 1) slab_kernel(SlabArgs a) {
   const long long total_in = a.nsl * slice_in;
   const char *gin = static_cast<const char *>(a.in);
   char *gout = static_cast<char *>(a.out);
-  const uint32_t tc = a.tmem_cols;  // accumulator columns per buffer
+  const uint32_t tc = a.tmem_cols;  // accumulator columns per group
 
   for (int r = tid; r < a.G * a.nb; r += kSlabThreads) row_n[r] = static_cast<uint16_t>((r / a.nb) * a.Rb + r % a.nb);
   if (tid == 0) {
-    for (int b = 0; b < 2; ++b) {
-      ptx::mbar_init(ptx::smem_u32(&bar_raw[b]), 1);
-      ptx::mbar_init(ptx::smem_u32(&bar_mma1[b]), 1);
-      ptx::mbar_init(ptx::smem_u32(&bar_mma2[b]), 1);
-      ptx::mbar_init(ptx::smem_u32(&bar_dfree[b]), 128);
+    for (int w = 0; w < kSlabGroups; ++w) {
+      ptx::mbar_init(ptx::smem_u32(&bar_raw[w]), 1);
+      ptx::mbar_init(ptx::smem_u32(&bar_mma[w]), 1);
     }
-    for (int w = 0; w < 3; ++w) ptx::mbar_init(ptx::smem_u32(&bar_fin[w]), 1);
     ptx::mbar_init_fence();
     abort_flag = 0;
   }
@@ -188,10 +188,11 @@ __global__ void __launch_bounds__(kSlabThreads, 1) slab_kernel(SlabArgs a) {
     for (int i = tid; i < a.szB2 / 16; i += kSlabThreads) reinterpret_cast<uint4 *>(sm + a.off_B2)[i] = srcB[i];
     const uint4 zero = make_uint4(0, 0, 0, 0);
     // padding rows and K chunks of the data operands stay zero for the whole kernel
-    for (int i = tid; i < 2 * a.szB1 / 16; i += kSlabThreads) reinterpret_cast<uint4 *>(sm + a.off_B1)[i] = zero;
-    for (int i = tid; i < 2 * a.G * a.szA2 / 16; i += kSlabThreads) reinterpret_cast<uint4 *>(sm + a.off_A2)[i] = zero;
+    for (int i = tid; i < ngroups * a.szB1 / 16; i += kSlabThreads) reinterpret_cast<uint4 *>(sm + a.off_B1)[i] = zero;
+    for (int i = tid; i < ngroups * a.G * a.szA2 / 16; i += kSlabThreads)
+      reinterpret_cast<uint4 *>(sm + a.off_A2)[i] = zero;
   }
-  if (warp == 0) ptx::tmem_alloc(ptx::smem_u32(&tmem_holder), 2 * tc);
+  if (warp == 0) ptx::tmem_alloc(ptx::smem_u32(&tmem_holder), a.tmem_alloc);
   ptx::fence_proxy_async();
   ptx::fence_before_sync();
   __syncthreads();
@@ -210,7 +211,7 @@ __global__ void __launch_bounds__(kSlabThreads, 1) slab_kernel(SlabArgs a) {
     }
   };
   auto aborted = [&]() { return *reinterpret_cast<volatile int *>(&abort_flag) != 0; };
-  // the bulk copy of step i's input covers [start & ~15, ceil16(end)), stopping
+  // the bulk copy of a step's input covers [start & ~15, ceil16(end)), stopping
   // at end & ~15 where ceil16(end) would pass the end of the tensor
   auto bulk_end = [&](long long end) {
     const long long up = (end + 15) & ~15LL;
@@ -218,38 +219,43 @@ __global__ void __launch_bounds__(kSlabThreads, 1) slab_kernel(SlabArgs a) {
   };
   auto step_of = [&](long long i) { return static_cast<long long>(blockIdx.x) + i * gridDim.x; };
 
-  if (wg == 2) {
-    // ---------------- producer: input copies, conversion, product 1 ----------------
-    bool raw_pending[2] = {false, false};
-    uint32_t raw_phase[2] = {0, 0};
+  if (wg < ngroups) {
+    uint8_t *sRaw = sm + a.off_raw + wg * a.szRaw;
+    uint8_t *sB1 = sm + a.off_B1 + wg * a.szB1;
+    uint8_t *sA2 = sm + a.off_A2 + wg * a.G * a.szA2;
+    uint8_t *sOut = sm + a.off_out + wg * a.szOut;
+    uint64_t *braw = &bar_raw[wg], *bmma = &bar_mma[wg];
+    const uint32_t tbuf = tmem + wg * tc;
+    const uint32_t lane_base = static_cast<uint32_t>((warp & 3) * 32) << 16;
+    const bool active = (warp & 3) * 32 < a.na;
+    const bool valid = lt < a.na;
+    uint32_t raw_phase = 0, mma_phase = 0;
+    bool raw_pending = false;
     auto issue_raw = [&](long long i) {
-      const int b = static_cast<int>(i & 1);
       const long long s0 = step_of(i) * a.G;
       const long long gv = min(static_cast<long long>(a.G), a.nsl - s0);
       const long long start = s0 * slice_in, end = start + gv * slice_in;
       const long long b0 = start & ~15LL, b1 = bulk_end(end);
       if (b1 > b0) {
-        const uint32_t bar = ptx::smem_u32(&bar_raw[b]);
-        ptx::mbar_expect_tx(bar, static_cast<uint32_t>(b1 - b0));
-        ptx::bulk_g2s(ptx::smem_u32(sm + a.off_raw + b * a.szRaw), gin + b0, static_cast<uint32_t>(b1 - b0), bar);
-        raw_pending[b] = true;
+        ptx::mbar_expect_tx(ptx::smem_u32(braw), static_cast<uint32_t>(b1 - b0));
+        ptx::bulk_g2s(ptx::smem_u32(sRaw), gin + b0, static_cast<uint32_t>(b1 - b0), ptx::smem_u32(braw));
+        raw_pending = true;
       }
     };
-    if (lt == 0) {
-      for (long long i = 0; i < 2 && i < nloc; ++i) issue_raw(i);
-    }
-    for (long long i = 0; i < nloc; ++i) {
-      const int b = static_cast<int>(i & 1);
+    auto mma_wait = [&]() {
+      wait(bmma, mma_phase);
+      mma_phase ^= 1u;
+    };
+    if (lt == 0 && wg < nloc) issue_raw(wg);
+    for (long long i = wg; i < nloc; i += ngroups) {
       const long long s0 = step_of(i) * a.G;
       const int gv = static_cast<int>(min(static_cast<long long>(a.G), a.nsl - s0));
       const long long start = s0 * slice_in, end = start + gv * slice_in;
       const long long b0 = start & ~15LL, b1 = bulk_end(end);
-      uint8_t *sRaw = sm + a.off_raw + b * a.szRaw;
-      uint8_t *sB1 = sm + a.off_B1 + b * a.szB1;
       if (b1 > b0) {
-        wait(&bar_raw[b], raw_phase[b]);
-        raw_phase[b] ^= 1u;
-        raw_pending[b] = false;
+        wait(braw, raw_phase);
+        raw_phase ^= 1u;
+        raw_pending = false;
       }
       {
         // the last < 16 bytes of the tensor when the bulk copy stopped short of them
@@ -260,83 +266,87 @@ __global__ void __launch_bounds__(kSlabThreads, 1) slab_kernel(SlabArgs a) {
           *reinterpret_cast<InT *>(sRaw + (off - b0)) = *reinterpret_cast<const InT *>(gin + off);
         }
       }
-      if (i >= 2) wait(&bar_mma1[b], static_cast<uint32_t>(((i - 2) >> 1) & 1));  // data operand b is free
-      ptx::named_sync(1, 128);
+      ptx::named_sync(1 + wg, 128);
       {
-        // items (row, 8-wide chunk), rows fastest across the threads; row = g * nb + b
+        // items (row, 8-wide chunk), rows fastest across the threads, two items
+        // per pass (both loaded before either is converted and stored)
         const int nrows = gv * a.nb;
         const int nchk = sizeof(InT) == 2 ? a.in_pitch / 8 : a.kpa / 8;
+        const int nitems = nrows * nchk;  // items it = ch * nrows + row
         const uint8_t *raw = sRaw + (start - b0);
-        int row = lt % nrows, ch = lt / nrows;
-        const int drow = 128 % nrows, dch = 128 / nrows;
-        for (; ch < nchk; row += drow, ch += dch) {
-          if (row >= nrows) {
-            row -= nrows;
-            ++ch;
-            if (ch >= nchk) break;
-          }
-          const int n = row_n[row];  // g * Rb + b for row = g * nb + b
-          uint8_t *dst = sB1 + ch * a.lbo_b1 + (n >> 3) * 128 + (n & 7) * 16;
+        auto do_item = [&](int ch, int row, bool load_only, float *v, uint4 *cp) {
           if constexpr (sizeof(InT) == 2) {
-            *reinterpret_cast<uint4 *>(dst) =
-                *reinterpret_cast<const uint4 *>(raw + (static_cast<size_t>(row) * a.in_pitch + ch * 8) * 2);
-          } else {
-            const InT *src = reinterpret_cast<const InT *>(raw) + static_cast<size_t>(row) * a.in_pitch + ch * 8;
-            float v[8];
-            if (ch * 8 + 8 <= a.na) {
-              load8_f32(src, v);
+            if (load_only) {
+              *cp = *reinterpret_cast<const uint4 *>(raw + (static_cast<size_t>(row) * a.in_pitch + ch * 8) * 2);
             } else {
-#pragma unroll
-              for (int j = 0; j < 8; ++j) v[j] = ch * 8 + j < a.na ? load1_f32(src + j) : 0.f;
+              const int n = row_n[row];
+              *reinterpret_cast<uint4 *>(sB1 + ch * a.lbo_b1 + (n >> 3) * 128 + (n & 7) * 16) = *cp;
             }
-            uint4 pk;
-            pk.x = ptx::pack_bf16(v[0], v[1]);
-            pk.y = ptx::pack_bf16(v[2], v[3]);
-            pk.z = ptx::pack_bf16(v[4], v[5]);
-            pk.w = ptx::pack_bf16(v[6], v[7]);
-            *reinterpret_cast<uint4 *>(dst) = pk;
+          } else {
+            if (load_only) {
+              const InT *src = reinterpret_cast<const InT *>(raw) + static_cast<size_t>(row) * a.in_pitch + ch * 8;
+              if (ch * 8 + 8 <= a.na) {
+                load8_f32(src, v);
+              } else {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) v[j] = ch * 8 + j < a.na ? load1_f32(src + j) : 0.f;
+              }
+            } else {
+              const int n = row_n[row];
+              uint4 pk;
+              pk.x = ptx::pack_bf16(v[0], v[1]);
+              pk.y = ptx::pack_bf16(v[2], v[3]);
+              pk.z = ptx::pack_bf16(v[4], v[5]);
+              pk.w = ptx::pack_bf16(v[6], v[7]);
+              *reinterpret_cast<uint4 *>(sB1 + ch * a.lbo_b1 + (n >> 3) * 128 + (n & 7) * 16) = pk;
+            }
+          }
+        };
+        // item it = ch * nrows + row; (ch0, row0) for it and (ch1, row1) for it + 128,
+        // both advanced by 256 items per pass without divisions
+        int ch0 = lt / nrows, row0 = lt - ch0 * nrows;
+        int ch1 = (lt + 128) / nrows, row1 = lt + 128 - ch1 * nrows;
+        const int dch = 256 / nrows, drow = 256 - dch * nrows;
+        for (int it = lt; it < nitems; it += 256) {
+          float v0[8], v1[8];
+          uint4 c0, c1;
+          const bool two = it + 128 < nitems;
+          do_item(ch0, row0, true, v0, &c0);
+          if (two) do_item(ch1, row1, true, v1, &c1);
+          do_item(ch0, row0, false, v0, &c0);
+          if (two) do_item(ch1, row1, false, v1, &c1);
+          ch0 += dch;
+          row0 += drow;
+          if (row0 >= nrows) {
+            row0 -= nrows;
+            ++ch0;
+          }
+          ch1 += dch;
+          row1 += drow;
+          if (row1 >= nrows) {
+            row1 -= nrows;
+            ++ch1;
           }
         }
       }
       ptx::fence_proxy_async();
-      ptx::named_sync(1, 128);
+      ptx::fence_before_sync();
+      ptx::named_sync(1 + wg, 128);
       if (lt == 0) {
-        // input buffer b is consumed: fetch step i + 2 into it
-        if (!aborted() && i + 2 < nloc) issue_raw(i + 2);
-        if (i >= 2) wait(&bar_dfree[b], static_cast<uint32_t>(((i - 2) >> 1) & 1));  // accumulator b is free
         ptx::fence_after_sync();
+        // the input buffer is consumed: fetch this group's next step into it
+        if (!aborted() && i + ngroups < nloc) issue_raw(i + ngroups);
         if (!aborted()) {
           const uint32_t a0 = ptx::smem_u32(sA), b0s = ptx::smem_u32(sB1);
           for (int kk = 0; kk < a.kpa / 16; ++kk) {
             const uint64_t ad = ptx::make_desc(a0 + kk * 2 * lbo_a, lbo_a, 128, 0);
             const uint64_t bd = ptx::make_desc(b0s + kk * 2 * a.lbo_b1, a.lbo_b1, 128, 0);
-            ptx::mma_bf16(tmem + b * tc, ad, bd, a.idesc1, kk > 0 ? 1u : 0u);
+            ptx::mma_bf16(tbuf, ad, bd, a.idesc1, kk > 0 ? 1u : 0u);
           }
-          ptx::mma_commit(ptx::smem_u32(&bar_mma1[b]));
+          ptx::mma_commit(ptx::smem_u32(bmma));
         }
       }
-    }
-    if (lt == 0) {
-      // every MMA this thread issued has completed; in-flight input copies land
-      ptx::mma_commit(ptx::smem_u32(&bar_fin[2]));
-      ptx::mbar_wait(ptx::smem_u32(&bar_fin[2]), 0);
-      for (int b = 0; b < 2; ++b)
-        if (raw_pending[b]) ptx::mbar_wait(ptx::smem_u32(&bar_raw[b]), raw_phase[b]);
-    }
-  } else {
-    // ---------------- consumer wg (0, 1): steps i with i % 2 == wg ----------------
-    const int b = wg;
-    uint8_t *sA2 = sm + a.off_A2 + b * a.G * a.szA2;
-    uint8_t *sOut = sm + a.off_out + b * a.szOut;
-    const uint32_t lane_base = static_cast<uint32_t>((warp & 3) * 32) << 16;
-    const uint32_t tbuf = tmem + b * tc;
-    const bool active = (warp & 3) * 32 < a.na;
-    const bool valid = lt < a.na;
-    for (long long i = b; i < nloc; i += 2) {
-      const uint32_t ph = static_cast<uint32_t>((i >> 1) & 1);
-      const long long s0 = step_of(i) * a.G;
-      const int gv = static_cast<int>(min(static_cast<long long>(a.G), a.nsl - s0));
-      wait(&bar_mma1[b], ph);
+      mma_wait();
       ptx::fence_after_sync();
       // epilogue 1: accumulator row (lane) -> K-major row of product 2's A operand
       if (active) {
@@ -372,8 +382,8 @@ __global__ void __launch_bounds__(kSlabThreads, 1) slab_kernel(SlabArgs a) {
       }
       ptx::fence_proxy_async();
       ptx::fence_before_sync();
-      if (lt == 0) ptx::bulk_wait_read<0>();  // this warpgroup's previous store has read its staging buffer
-      ptx::named_sync(2 + b, 128);
+      if (lt == 0) ptx::bulk_wait_read<0>();  // this group's previous store has read its staging buffer
+      ptx::named_sync(1 + wg, 128);
       if (lt == 0) {
         ptx::fence_after_sync();
         if (!aborted()) {
@@ -386,10 +396,10 @@ __global__ void __launch_bounds__(kSlabThreads, 1) slab_kernel(SlabArgs a) {
               ptx::mma_bf16(tbuf + g * a.Rb, ad, bd, a.idesc2, kk > 0 ? 1u : 0u);
             }
           }
-          ptx::mma_commit(ptx::smem_u32(&bar_mma2[b]));
+          ptx::mma_commit(ptx::smem_u32(bmma));
         }
       }
-      wait(&bar_mma2[b], ph);
+      mma_wait();
       ptx::fence_after_sync();
       // epilogue 2: accumulator row (lane) = output row of the slice
       const long long ostart = s0 * slice_out, oend = ostart + gv * slice_out;
@@ -437,11 +447,9 @@ __global__ void __launch_bounds__(kSlabThreads, 1) slab_kernel(SlabArgs a) {
           }
         }
       }
-      // accumulator b may be overwritten by the product 1 of step i + 2
-      ptx::fence_before_sync();
-      ptx::mbar_arrive(ptx::smem_u32(&bar_dfree[b]));
       ptx::fence_proxy_async();
-      ptx::named_sync(2 + b, 128);
+      ptx::fence_before_sync();
+      ptx::named_sync(1 + wg, 128);
       {
         // bulk store of the 16-byte aligned middle; plain stores for the ends
         const long long c0 = (ostart + 15) & ~15LL, c1 = oend & ~15LL;
@@ -471,14 +479,14 @@ __global__ void __launch_bounds__(kSlabThreads, 1) slab_kernel(SlabArgs a) {
       }
     }
     if (lt == 0) {
+      // in-flight stores, MMAs and input copies finish before the buffers go away
       ptx::bulk_wait<0>();
-      ptx::mma_commit(ptx::smem_u32(&bar_fin[b]));
-      ptx::mbar_wait(ptx::smem_u32(&bar_fin[b]), 0);
+      if (raw_pending) ptx::mbar_wait(ptx::smem_u32(braw), raw_phase);
     }
   }
   ptx::fence_before_sync();
   __syncthreads();
-  if (warp == 0) ptx::tmem_dealloc(tmem, 2 * tc);
+  if (warp == 0) ptx::tmem_dealloc(tmem, a.tmem_alloc);
 }
 
 // ---------------------------------------------------------------------------
@@ -786,11 +794,13 @@ int ctas_per_sm(int smem) { return std::max(1, std::min(kMaxCtasPerSM, kSmemPerS
 // last K chunk past its end.
 int a_slack(int ra) { return (128 - ra) * 16; }
 
-// Shared-memory layout of a slab kernel with G slices per step (two buffers of
-// every per-step operand); returns the dynamic size (0 if it does not fit).
-int slab_layout(SlabArgs &s, int G, size_t in_size, size_t out_size) {
+// Shared-memory layout of a slab kernel with G slices per step and `groups`
+// warpgroup chains (one set of per-step buffers each); returns the dynamic size
+// (0 if it does not fit).
+int slab_layout(SlabArgs &s, int G, int groups, size_t in_size, size_t out_size) {
   auto up16 = [](long long x) { return static_cast<int>((x + 15) / 16 * 16); };
   s.G = G;
+  s.groups = groups;
   s.szA = s.kpa / 8 * s.ra * 16;
   s.szB2 = s.Rb / 8 * s.Rb * 16;
   s.lbo_b1 = static_cast<uint32_t>(G * s.Rb * 16);
@@ -804,37 +814,46 @@ int slab_layout(SlabArgs &s, int G, size_t in_size, size_t out_size) {
   s.off_B2 = off;
   off += up1024(s.szB2);
   s.off_B1 = off;
-  off += up1024(2LL * s.szB1);
+  off += up1024(static_cast<long long>(groups) * s.szB1);
   s.off_A2 = off;
-  off += up1024(2LL * G * s.szA2 + a_slack(s.ra));
+  off += up1024(static_cast<long long>(groups) * G * s.szA2 + a_slack(s.ra));
   s.off_raw = off;
-  off += up1024(2LL * s.szRaw);
+  off += up1024(static_cast<long long>(groups) * s.szRaw);
   s.off_out = off;
-  off += up1024(2LL * s.szOut);
+  off += up1024(static_cast<long long>(groups) * s.szOut);
   const int total = off + 1024;  // alignment of the dynamic base
   return total + kStaticSmem <= kSmemLimit ? total : 0;
 }
 
-// Slices per step: the largest G with G * Rb <= 256 whose buffers fit.
+// Three warpgroup chains if their buffers fit, else two; then the largest G
+// (G * Rb <= 256, and <= 128 with three chains: their accumulators share the
+// 512 tensor-memory columns) that fits.
 template <typename InT, typename OutT>
 cudaError_t plan_slab(SlabPlan &pl, SlabArgs base, long long nsl, int sms) {
-  const int gmax = static_cast<int>(std::min<long long>(kSlabMaxN / base.Rb, nsl));
-  for (int G = gmax; G >= 1; --G) {
-    SlabArgs s = base;
-    const int smem = slab_layout(s, G, sizeof(InT), sizeof(OutT));
-    if (smem == 0) continue;
-    s.nsl = nsl;
-    s.inv_nb = 1.0f / static_cast<float>(s.nb);
-    s.idesc1 = ptx::idesc_bf16(128, G * s.Rb, 0);
-    s.idesc2 = ptx::idesc_bf16(128, s.Rb, 0);
-    uint32_t cols = 32;
-    while (cols < static_cast<uint32_t>(G * s.Rb)) cols *= 2;
-    s.tmem_cols = cols;
-    pl.args = s;
-    pl.smem = smem;
-    const long long nsteps = (nsl + G - 1) / G;
-    pl.grid = static_cast<int>(std::min<long long>(nsteps, sms));
-    return cudaFuncSetAttribute(slab_kernel<InT, OutT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  for (int groups = kSlabGroups; groups >= 2; --groups) {
+    const int maxn = groups == 3 ? 128 : kSlabMaxN;
+    const int gmax = static_cast<int>(std::min<long long>(maxn / base.Rb, nsl));
+    for (int G = gmax; G >= 1; --G) {
+      SlabArgs s = base;
+      const int smem = slab_layout(s, G, groups, sizeof(InT), sizeof(OutT));
+      if (smem == 0) continue;
+      s.nsl = nsl;
+      s.inv_nb = 1.0f / static_cast<float>(s.nb);
+      s.idesc1 = ptx::idesc_bf16(128, G * s.Rb, 0);
+      s.idesc2 = ptx::idesc_bf16(128, s.Rb, 0);
+      uint32_t cols = 32;
+      while (cols < static_cast<uint32_t>(G * s.Rb)) cols *= 2;
+      s.tmem_cols = cols;
+      uint32_t alloc = 32;
+      while (alloc < static_cast<uint32_t>(groups) * cols) alloc *= 2;
+      if (alloc > 512) continue;
+      s.tmem_alloc = alloc;
+      pl.args = s;
+      pl.smem = smem;
+      const long long nsteps = (nsl + G - 1) / G;
+      pl.grid = static_cast<int>(std::min<long long>(nsteps, sms));
+      return cudaFuncSetAttribute(slab_kernel<InT, OutT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    }
   }
   return cudaErrorInvalidConfiguration;
 }
