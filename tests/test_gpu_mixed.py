@@ -94,6 +94,26 @@ def test_operand_rounding_bit_exact():
 
 
 @pytest.mark.parametrize("form", ["bf16", "tf32"])
+@pytest.mark.parametrize("d,p,n_el,kw,batch", [
+    (3, 3, [4, 7, 5], dict(T=1.3, p_t=2, n_el_t=6), 2),
+    (3, 2, [9, 3, 6], dict(T=0.7, p_t=4, n_el_t=3), 1),
+    (2, 4, [11, 5], dict(T=2.0, p_t=1, n_el_t=9), 3),
+    (2, 3, [40, 7], dict(T=1.0), 1)])
+def test_tc_precond_anisotropic_matches_model(form, d, p, n_el, kw, batch):
+    """Different sizes per direction (so the slab kernels' two directions and the
+    streaming passes see different n), other time degrees and T != 1."""
+    prob = STProblem(d, p, n_el, **kw)
+    fd = FD(prob)
+    S = _solver(d, p, n_el, precision=form, batch=batch, **kw)
+    r = synth.uniform(prob.N, 700 + d + p, batch=batch).reshape(batch, prob.N)
+    z = S.apply_precond(torch.from_numpy(r).cuda()).cpu().numpy().reshape(batch, prob.N)
+    for b in range(batch):
+        model = mixed.apply_mixed(fd, r[b], form, _bwd_order(form, d))
+        assert _rel(z[b], model) <= TOL_MODEL[form], _rel(z[b], model)
+        assert _rel(z[b], fd.apply(r[b])) <= TOL_EXACT[form]
+
+
+@pytest.mark.parametrize("form", ["bf16", "tf32"])
 def test_tc_precond_full_size_cfg4(form):
     prob = STProblem(3, 3, 64)
     fd = FD(prob)
