@@ -62,6 +62,7 @@ constexpr int kSlabMaxN = 256;         // columns of the slab kernel's first pro
 constexpr int kTileN = 128;            // columns per streaming tile (MMA N)
 constexpr int kAtomCols = 64;          // BF16 columns per 128-byte swizzle atom
 constexpr int kAtoms = kTileN / kAtomCols;
+constexpr int kStages = 3;             // input stages of a streaming kernel (outputs reuse them)
 constexpr int kSmemLimit = 227 * 1024;   // per CTA
 constexpr int kSmemPerSM = 228 * 1024;   // per SM
 constexpr int kCtaReserve = 1024 + 256;  // reserved per CTA + static shared memory
@@ -500,10 +501,9 @@ struct StreamArgs {
   const float *lam_t;           // TIME: >= 128 entries
   const float *lam_s;           // TIME: nct * 256 entries (padding 1)
   int n, kp, nouter, nct, ra;    // ra = ceil8(n) stored rows of the A images
-  int nstg;                     // staging buffers (1 or 2)
   long long cols;               // S (or S3): columns of the tensor
-  uint32_t atom_in, atom_out;   // bytes per 64-column box: kp * 128, ceil8(n) * 128
-  int off_A, off_A2, off_stage, off_stg;
+  uint32_t atom_in;             // bytes per 64-column box: kp * 128
+  int off_A, off_A2, off_stage, off_lam;  // off_lam: TIME, kTileN floats per stage
   int szA;
   uint32_t idesc;
   int *err;
@@ -514,28 +514,27 @@ __global__ void __launch_bounds__(kThreads, 2)
     stream_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tout,
                   StreamArgs a) {
   extern __shared__ uint8_t smem_dyn[];
-  __shared__ __align__(8) uint64_t bar_load[2];
+  __shared__ __align__(8) uint64_t bar_load[kStages];
   __shared__ __align__(8) uint64_t bar_mma;
   __shared__ uint32_t tmem_holder;
   __shared__ int ok;
   uint8_t *sm = align1024(smem_dyn);
   uint8_t *sA = sm + a.off_A, *sA2 = sm + a.off_A2;
-  uint8_t *stage0 = sm + a.off_stage, *stg0 = sm + a.off_stg;
-  const uint32_t sz_stage = kAtoms * a.atom_in, sz_stg = kAtoms * a.atom_out;
+  uint8_t *stage0 = sm + a.off_stage;
+  const uint32_t sz_stage = kAtoms * a.atom_in;
   const int tid = threadIdx.x, warp = tid >> 5;
   const uint32_t lb0 = ptx::smem_u32(&bar_load[0]), mb = ptx::smem_u32(&bar_mma);
   const long long ntiles = static_cast<long long>(a.nouter) * a.nct;
 
   if (tid == 0) {
-    ptx::mbar_init(lb0, 1);
-    ptx::mbar_init(lb0 + 8, 1);
+    for (int k = 0; k < kStages; ++k) ptx::mbar_init(lb0 + 8 * k, 1);
     ptx::mbar_init(mb, 1);
     ptx::mbar_init_fence();
     ok = 1;
   }
   {
     const uint4 zero = make_uint4(0, 0, 0, 0);
-    for (uint32_t i = tid; i < 2 * sz_stage / 16; i += kThreads) reinterpret_cast<uint4 *>(stage0)[i] = zero;
+    for (uint32_t i = tid; i < kStages * sz_stage / 16; i += kThreads) reinterpret_cast<uint4 *>(stage0)[i] = zero;
     const uint4 *src = reinterpret_cast<const uint4 *>(a.imgA);
     for (int i = tid; i < a.szA / 16; i += kThreads) reinterpret_cast<uint4 *>(sA)[i] = src[i];
     if (TIME) {
@@ -562,8 +561,10 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int o = static_cast<int>(t / a.nct), c0 = static_cast<int>(t % a.nct) * kTileN;
     const uint32_t bar = lb0 + 8 * s, dst = ptx::smem_u32(stage0) + s * sz_stage;
     const int nb = boxes(c0);
-    ptx::mbar_expect_tx(bar, nb * a.atom_in);
+    ptx::mbar_expect_tx(bar, nb * a.atom_in + (TIME ? kTileN * 4 : 0));
     for (int at = 0; at < nb; ++at) ptx::tma_load_3d(dst + at * a.atom_in, &tin, c0 + at * kAtomCols, 0, o, bar);
+    // the tile's lambda_s (padded to whole tiles) travels with it
+    if (TIME) ptx::bulk_g2s(ptx::smem_u32(sm + a.off_lam) + s * kTileN * 4, a.lam_s + c0, kTileN * 4, bar);
   };
   auto issue_mma = [&](const uint8_t *A, int s) {
     const uint32_t a0 = ptx::smem_u32(A), b0 = ptx::smem_u32(stage0) + s * sz_stage;
@@ -587,8 +588,8 @@ __global__ void __launch_bounds__(kThreads, 2)
 
   uint32_t mma_phase = 0;
   bool mma_pending = false;                        // thread 0: for the error path
-  bool load_pending[2] = {false, false};
-  uint32_t load_phase[2] = {0, 0};
+  bool load_pending[kStages] = {};
+  uint32_t load_phase[kStages] = {};
   if (tid == 0) {
     for (int i = 0; i < 2; ++i) {
       const long long t = blockIdx.x + static_cast<long long>(i) * gridDim.x;
@@ -602,7 +603,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   const bool active = warp * 32 < a.n;
   const bool valid = tid < a.n;
   for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
-    const int s = it & 1;
+    const int s = it % kStages;
     const int o = static_cast<int>(t / a.nct), c0 = static_cast<int>(t % a.nct) * kTileN;
     uint8_t *stage = stage0 + s * sz_stage;
     if (ptx::mbar_wait(lb0 + 8 * s, load_phase[s])) {
@@ -634,11 +635,11 @@ __global__ void __launch_bounds__(kThreads, 2)
           uint32_t r[64];
           load_half(half, r);
           if (!valid) continue;
-          const float4 *ls4 = reinterpret_cast<const float4 *>(a.lam_s + c0 + half * 64);
+          const float4 *ls4 = reinterpret_cast<const float4 *>(sm + a.off_lam + s * kTileN * 4) + half * 16;
 #pragma unroll
           for (int qq = 0; qq < 8; ++qq) {
             const int q = half * 8 + qq;
-            const float4 l0 = __ldg(ls4 + 2 * qq), l1 = __ldg(ls4 + 2 * qq + 1);
+            const float4 l0 = ls4[2 * qq], l1 = ls4[2 * qq + 1];
             const uint32_t *u = r + 8 * qq;
             uint4 pk;
             pk.x = ptx::pack_bf16(__fdividef(__uint_as_float(u[0]), lt + l0.x), __fdividef(__uint_as_float(u[1]), lt + l0.y));
@@ -665,21 +666,9 @@ __global__ void __launch_bounds__(kThreads, 2)
       }
       ptx::fence_after_sync();
     }
-    if (tid == 0) {
-      // the tile's stage is consumed: fetch two tiles ahead; and the staging
-      // buffer used two tiles ago must have been read by its store
-      const long long tn = t + 2LL * gridDim.x;
-      if (ok && !mma_pending && tn < ntiles) {
-        issue_load(tn, s);
-        load_pending[s] = true;
-      }
-      if (a.nstg == 2)
-        ptx::bulk_wait_read<1>();
-      else
-        ptx::bulk_wait_read<0>();
-    }
-    __syncthreads();
-    uint8_t *stg = stg0 + (a.nstg == 2 ? s : 0) * sz_stg;
+    // the products have read the stage: the output rows go into it (same
+    // swizzled box layout) and the TMA store reads them from there
+    uint8_t *stg = stage;
     if (active) {
       for (int half = 0; half < kTileN / 64; ++half) {
         uint32_t r[64];
@@ -694,7 +683,7 @@ __global__ void __launch_bounds__(kThreads, 2)
           pk.y = ptx::pack_bf16(__uint_as_float(u[2]), __uint_as_float(u[3]));
           pk.z = ptx::pack_bf16(__uint_as_float(u[4]), __uint_as_float(u[5]));
           pk.w = ptx::pack_bf16(__uint_as_float(u[6]), __uint_as_float(u[7]));
-          *reinterpret_cast<uint4 *>(box_addr(stg + (q >> 3) * a.atom_out, tid, q & 7)) = pk;
+          *reinterpret_cast<uint4 *>(box_addr(stg + (q >> 3) * a.atom_in, tid, q & 7)) = pk;
         }
       }
     }
@@ -704,15 +693,24 @@ __global__ void __launch_bounds__(kThreads, 2)
     if (tid == 0) {
       const uint32_t src = ptx::smem_u32(stg);
       const int nb = boxes(c0);
-      for (int at = 0; at < nb; ++at) ptx::tma_store_3d(&tout, c0 + at * kAtomCols, 0, o, src + at * a.atom_out);
+      for (int at = 0; at < nb; ++at) ptx::tma_store_3d(&tout, c0 + at * kAtomCols, 0, o, src + at * a.atom_in);
       ptx::bulk_commit();
+      // fetch two tiles ahead into the stage of the previous tile, once that
+      // tile's store has read it (at most this tile's store still reads)
+      const long long tn = t + 2LL * gridDim.x;
+      if (ok && !mma_pending && tn < ntiles) {
+        const int sn = (it + 2) % kStages;
+        ptx::bulk_wait_read<1>();
+        issue_load(tn, sn);
+        load_pending[sn] = true;
+      }
     }
   }
   if (tid == 0) {
     ptx::bulk_wait<0>();
     if (!ok) {
       *reinterpret_cast<volatile int *>(a.err) = 1;
-      for (int k = 0; k < 2; ++k)
+      for (int k = 0; k < kStages; ++k)
         if (load_pending[k]) ptx::mbar_wait(lb0 + 8 * k, load_phase[k]);
       if (mma_pending) ptx::mbar_wait(mb, mma_phase);
     }
@@ -895,25 +893,17 @@ cudaError_t plan_stream(StreamPlan &pl, int n, long long cols, long long outer, 
   s.nct = static_cast<int>((cols + kTileN - 1) / kTileN);
   s.cols = cols;
   s.atom_in = static_cast<uint32_t>(s.kp) * 128;
-  s.atom_out = static_cast<uint32_t>(s.ra) * 128;
   s.szA = s.kp / 8 * s.ra * 16;
-  auto layout = [&](int nstg) {
-    int off = 0;
-    s.nstg = nstg;
-    s.off_stage = off;  // stages first: every operand address stays inside the allocation
-    off += 2 * kAtoms * static_cast<int>(s.atom_in);
-    s.off_stg = off;
-    off += nstg * kAtoms * static_cast<int>(s.atom_out);
-    s.off_A = off;
-    off += up1024(s.szA + a_slack(s.ra));
-    s.off_A2 = off;
-    if (TIME) off += up1024(s.szA + a_slack(s.ra));
-    return off + 1024;
-  };
-  // two staging buffers unless one buffer lets more CTAs share an SM
-  pl.smem = layout(2);
-  if (ctas_per_sm(layout(1)) > ctas_per_sm(pl.smem)) pl.smem = layout(1);
-  else pl.smem = layout(2);
+  int off = 0;
+  s.off_stage = off;  // stages first: every operand address stays inside the allocation
+  off += kStages * kAtoms * static_cast<int>(s.atom_in);
+  s.off_A = off;
+  off += up1024(s.szA + a_slack(s.ra));
+  s.off_A2 = off;
+  if (TIME) off += up1024(s.szA + a_slack(s.ra));
+  s.off_lam = off;
+  if (TIME) off += kStages * kTileN * 4;
+  pl.smem = off + 1024;
   if (pl.smem + kStaticSmem > kSmemLimit) {
     err = "tensor-core preconditioner: streaming tile does not fit in shared memory";
     return cudaErrorInvalidConfiguration;
