@@ -183,9 +183,13 @@ def timed_solves(S, F, u, tol, steps, warmup, world, timing):
 
 
 # ncu DRAM bytes (read + write) per operation on this workload, from the
-# captures summarised under profiles/; None where no capture of the current
-# kernels exists.
-TRAFFIC = {}
+# captures summarised under profiles/ (ncu flushes the caches before every
+# kernel, so intermediate tensors that stay in L2 in a normal run count as DRAM
+# reads there); None where no capture of the current kernels exists.
+TRAFFIC = {
+    # fused BF16 FD apply with FP32 in/out: 5 kernels, 234.8 MB read + 19.1 MB written
+    ("precond", "bf16", True): 253888256,
+}
 
 
 def roofline_entry(phase, ms, count, S, p, peaks, refine):
