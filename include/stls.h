@@ -72,7 +72,11 @@ typedef struct {
                        and corrects u with an inner flexible CG in FP32
                        (FP32 vectors and A p, tensor-core preconditioner, inner
                        products accumulated in FP64) that reduces its scaled
-                       residual by inner_tol. */
+                       residual by inner_tol.  With d = 2, 3 an outer step whose
+                       predicted residual ||r|| max(inner residual, 4e-4) exceeds
+                       both 100 tol and 1e-8 takes a provisional residual with
+                       the double-float A x (stls_apply_A_df); the FP64 residual
+                       decides every convergence test. */
   double inner_tol; /* relative tolerance of the inner solves.  0: adaptive:
                        the reduction R = tol ||F|| / ||r|| still needed is split
                        over K = ceil(log R / log 1e-3) outer steps, inner
@@ -86,7 +90,10 @@ typedef struct {
   double rel_res;       /* ||r_k|| / ||F|| of the residual the stopping test used:
                            recursively updated (refine = 0) or F - A u in FP64 (refine = 1) */
   double true_rel_res;  /* ||F - A u|| / ||F|| recomputed in FP64 at exit */
-  int outer;            /* FP64 residual evaluations of the refinement loop (0 if refine = 0) */
+  int outer;            /* outer steps of the refinement loop, each ended by a residual
+                           evaluation (0 if refine = 0) */
+  int outer_df;         /* of those, provisional residuals in double-float arithmetic
+                           (stls_apply_A_df); the FP64 residual confirmed the last one */
 } stls_solve_info;
 
 /* Create a solver context: builds the 1D Galerkin matrices (Sec. 4.1-4.2) and
@@ -113,6 +120,17 @@ int stls_sizes(const stls_ctx *ctx, int *n_s, int *n_t, long long *n_dof, int *b
 /* y = A x for the batch (Eq. A_kron: A = K_t x M_s + M_t x J_s + W_t x L_s),
  * matrix-free by banded mode products in FP64.  x, y: device, B x N. */
 int stls_apply_A(stls_ctx *ctx, const double *x, double *y);
+
+/* y = A x as stls_apply_A, in double-float arithmetic: every FP64 value is
+ * carried as the unevaluated sum of two FP32 values (about 48 significant
+ * bits) and every product and sum runs on the FP32 pipe.  This is the
+ * operator of the refinement form's provisional outer residuals (the FP64
+ * residual confirms convergence).  Accurate while x, A x and the
+ * intermediate products stay inside the FP32 normal range (about 1e-38 to
+ * 3e38 in magnitude).  x, y: device, B x N, must not overlap.  Errors:
+ * STLS_EINVAL unless the context has refine = 1, d = 2 or 3 and degrees
+ * 1..5 (the fused A x). */
+int stls_apply_A_df(stls_ctx *ctx, const double *x, double *y);
 
 /* z = P^{-1} r for the batch by fast diagonalization (Eq. preconditioner,
  * Algorithm 1, steps 2-4) in the context's precision.  r, z: device, B x N;

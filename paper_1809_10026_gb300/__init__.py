@@ -118,6 +118,15 @@ class Solver:
         _check(self.lib.stls_apply_A(self.ctx, self._ptr(x), self._ptr(y)), self.ctx)
         return y
 
+    def apply_A_df(self, x, out=None):
+        """A x in double-float arithmetic (FP32 pairs), as the refinement form's
+        provisional outer residuals use it; refinement contexts only."""
+        x = self._vec(x, self.N, "x")
+        y = self._out(x.shape, self.N) if out is None else out
+        self._stream()
+        _check(self.lib.stls_apply_A_df(self.ctx, self._ptr(x), self._ptr(y)), self.ctx)
+        return y
+
     def apply_precond(self, r, out=None):
         r = self._vec(r, self.N, "r")
         z = self._out(r.shape, self.N) if out is None else out

@@ -12,7 +12,7 @@ PRECISION = {"fp64": 0, "tf32": 1, "bf16": 2}
 FACTOR = {"mass": 0, "stiff": 1, "bilap": 2, "eigvec": 3, "eigval": 4, "end": 5, "integral": 6}
 
 EXPORTS = ["stls_create", "stls_destroy", "stls_last_error", "stls_set_stream", "stls_sizes",
-           "stls_apply_A", "stls_apply_precond", "stls_solve", "stls_solve_host", "stls_apply_lift",
+           "stls_apply_A", "stls_apply_A_df", "stls_apply_precond", "stls_solve", "stls_solve_host", "stls_apply_lift",
            "stls_lift_adjoint", "stls_get_factor", "stls_host_factor", "stls_launch_count",
            "stls_enable_timing", "stls_phase_times", "stls_apply_precond_noalloc", "stls_round_bf16"]
 
@@ -26,11 +26,12 @@ class Params(ctypes.Structure):
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("status", ctypes.c_int), ("rel_res", ctypes.c_double),
-                ("true_rel_res", ctypes.c_double), ("outer", ctypes.c_int)]
+                ("true_rel_res", ctypes.c_double), ("outer", ctypes.c_int), ("outer_df", ctypes.c_int)]
 
     def as_dict(self):
         return {"iters": self.iters, "status": STATUS_NAMES.get(self.status, str(self.status)),
-                "rel_res": self.rel_res, "true_rel_res": self.true_rel_res, "outer": self.outer}
+                "rel_res": self.rel_res, "true_rel_res": self.true_rel_res, "outer": self.outer,
+                "outer_df": self.outer_df}
 
 
 _lib = None
@@ -57,6 +58,7 @@ def load():
     lib.stls_sizes.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_int)]
     lib.stls_apply_A.argtypes = [vp, vp, vp]
+    lib.stls_apply_A_df.argtypes = [vp, vp, vp]
     lib.stls_apply_precond.argtypes = [vp, vp, vp]
     lib.stls_solve.argtypes = [vp, vp, vp, ctypes.c_double, i, ctypes.POINTER(SolveInfo)]
     lib.stls_solve_host.argtypes = [vp, vp, vp, ctypes.c_double, i, ctypes.POINTER(SolveInfo)]

@@ -20,6 +20,7 @@
 #include <cstring>
 
 #include "kernels.h"
+#include "tc_ptx.cuh"
 
 namespace stls {
 namespace {
@@ -36,6 +37,12 @@ __device__ __forceinline__ void unpack(const double2 &q, double *e) {
   e[0] = q.x;
   e[1] = q.y;
 }
+__device__ __forceinline__ void unpack(const float4 &q, dfloat *e) {
+  e[0].h = q.x;
+  e[0].l = q.y;
+  e[1].h = q.z;
+  e[1].l = q.w;
+}
 template <typename T>
 struct Vec16;
 template <>
@@ -45,6 +52,10 @@ struct Vec16<float> {
 template <>
 struct Vec16<double> {
   using V = double2;
+};
+template <>
+struct Vec16<dfloat> {
+  using V = float4;
 };
 
 // The W coefficients of one band row, read as whole 16-byte vectors (rows are
@@ -69,6 +80,45 @@ __device__ __forceinline__ T band_dot(const T (&c)[W], const T (&v)[W], T acc) {
 #pragma unroll
   for (int w = 0; w < W; ++w) acc = fma(c[w], v[w], acc);
   return acc;
+}
+
+// Double-float form of band_dot: acc + sum_w c_w v_w.  Each product of the
+// high parts is split exactly into p + e by one FMA (Dekker's product), p is
+// added to the running high sum by Knuth's TwoSum, and e, the TwoSum errors
+// and the cross terms c.h v.l + c.l v.h collect in one FP32 low sum; the pair
+// is renormalised once at the end (Fast2Sum).  The dropped c.l v.l is below
+// 2^-48 of the product.  Explicit _rn operations keep the compiler from
+// contracting the error-free transformations into FMAs.
+template <int W>
+__device__ __forceinline__ dfloat band_dot(const dfloat (&c)[W], const dfloat (&v)[W], dfloat acc) {
+  float s = acc.h, lo = acc.l;
+#pragma unroll
+  for (int w = 0; w < W; ++w) {
+    const float p = __fmul_rn(c[w].h, v[w].h);
+    float e = __fmaf_rn(c[w].h, v[w].h, -p);
+    e = __fmaf_rn(c[w].h, v[w].l, e);
+    e = __fmaf_rn(c[w].l, v[w].h, e);
+    const float t = __fadd_rn(s, p);
+    const float z = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+    lo = __fadd_rn(lo, __fadd_rn(e, err));
+    s = t;
+  }
+  dfloat r;
+  r.h = __fadd_rn(s, lo);
+  r.l = __fsub_rn(lo, __fsub_rn(r.h, s));
+  return r;
+}
+
+// a += b in double-float arithmetic (TwoSum of the high parts, then Fast2Sum).
+__device__ __forceinline__ dfloat &operator+=(dfloat &a, const dfloat &b) {
+  const float t = __fadd_rn(a.h, b.h);
+  const float z = __fsub_rn(t, a.h);
+  const float err = __fadd_rn(__fsub_rn(a.h, __fsub_rn(t, z)), __fsub_rn(b.h, z));
+  const float lo = __fadd_rn(__fadd_rn(a.l, b.l), err);
+  a.h = __fadd_rn(t, lo);
+  a.l = __fsub_rn(lo, __fsub_rn(a.h, t));
+  return a;
 }
 
 template <typename T, int W>
@@ -431,6 +481,43 @@ __global__ void __launch_bounds__(kAThreads) tpass_kernel(const __grid_constant_
   }
 }
 
+// ---- double-float images of FP64 vectors ------------------------------------------------
+constexpr int kDfThreads = 256;
+
+__global__ void __launch_bounds__(kDfThreads)
+    df_split_kernel(const double *__restrict__ x, dfloat *__restrict__ y, long long N, const CGState *scale) {
+  const int b = blockIdx.y;
+  const int k = scale != nullptr ? ptx::df_scale_exp(scale[b].nF2) : 0;
+  const double *xb = x + static_cast<size_t>(b) * N;
+  dfloat *yb = y + static_cast<size_t>(b) * N;
+  for (long long i = blockIdx.x * static_cast<long long>(kDfThreads) + threadIdx.x; i < N;
+       i += static_cast<long long>(gridDim.x) * kDfThreads) {
+    const double v = ptx::scale_f64(xb[i], -k);
+    dfloat o;
+    o.h = ptx::f64_to_f32_rn(v);
+    o.l = ptx::f64_to_f32_rn(v - ptx::f32_to_f64(o.h));  // v - h is exact in FP64
+    yb[i] = o;
+  }
+}
+
+__global__ void __launch_bounds__(kDfThreads)
+    df_join_kernel(const dfloat *__restrict__ y, double *__restrict__ x, long long N, const CGState *scale) {
+  const int b = blockIdx.y;
+  const int k = scale != nullptr ? ptx::df_scale_exp(scale[b].nF2) : 0;
+  const dfloat *yb = y + static_cast<size_t>(b) * N;
+  double *xb = x + static_cast<size_t>(b) * N;
+  for (long long i = blockIdx.x * static_cast<long long>(kDfThreads) + threadIdx.x; i < N;
+       i += static_cast<long long>(gridDim.x) * kDfThreads) {
+    const dfloat o = yb[i];
+    xb[i] = ptx::scale_f64(ptx::f32_to_f64(o.h) + ptx::f32_to_f64(o.l), k);
+  }
+}
+
+unsigned df_grid(long long N) {
+  const long long g = (N + kDfThreads - 1) / kDfThreads;
+  return static_cast<unsigned>(g < 1 ? 1 : (g > 152 * 16 ? 152 * 16 : g));
+}
+
 long long blocks_for(long long cols) { return (cols + kAThreads - 1) / kAThreads; }
 
 template <typename T, int P>
@@ -598,8 +685,21 @@ void toeplitz_rows(const T *const *bands, int nbands, int n, int stride, int *lo
 }
 template void toeplitz_rows<double>(const double *const *, int, int, int, int *, int *);
 template void toeplitz_rows<float>(const float *const *, int, int, int, int *, int *);
+template void toeplitz_rows<dfloat>(const dfloat *const *, int, int, int, int *, int *);
 
 template cudaError_t launch_fused_A<double>(const FusedA<double> &, const double *, double *, cudaStream_t);
 template cudaError_t launch_fused_A<float>(const FusedA<float> &, const float *, float *, cudaStream_t);
+template cudaError_t launch_fused_A<dfloat>(const FusedA<dfloat> &, const dfloat *, dfloat *, cudaStream_t);
+
+cudaError_t launch_df_split(const double *x, dfloat *y, long long N, int B, const CGState *scale, cudaStream_t s) {
+  if (N < 0 || B < 1 || B > 65535) return cudaErrorInvalidValue;
+  if (N > 0) df_split_kernel<<<dim3(df_grid(N), B), kDfThreads, 0, s>>>(x, y, N, scale);
+  return cudaGetLastError();
+}
+cudaError_t launch_df_join(const dfloat *y, double *x, long long N, int B, const CGState *scale, cudaStream_t s) {
+  if (N < 0 || B < 1 || B > 65535) return cudaErrorInvalidValue;
+  if (N > 0) df_join_kernel<<<dim3(df_grid(N), B), kDfThreads, 0, s>>>(y, x, N, scale);
+  return cudaGetLastError();
+}
 
 }  // namespace stls

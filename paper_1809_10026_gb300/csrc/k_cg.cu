@@ -9,6 +9,7 @@
 #include <cmath>
 
 #include "kernels.h"
+#include "tc_ptx.cuh"
 
 namespace stls {
 
@@ -114,6 +115,7 @@ __global__ void __launch_bounds__(kThreads)
     s.nF2 = tot[0];
     s.rr = tot[0];
     s.iters = 0;
+    s.df_iters = 0;
     s.status = 0;
     s.rel_res = 1.0;
     s.true_rr = 0.0;
@@ -338,10 +340,11 @@ __global__ void __launch_bounds__(kThreads)
     ub[i] = fma(s, static_cast<double>(db[i]), ub[i]);
 }
 
-// r64 = F - A u in FP64 and the outer convergence test on ||r64|| / ||F||.
+// r64 = F - A u in FP64 and the outer convergence test on ||r64|| / ||F||
+// (`count`: whether this residual ends an outer step).
 __global__ void __launch_bounds__(kThreads)
     ir_residual_kernel(const double *__restrict__ F, const double *__restrict__ Au, double *__restrict__ r64,
-                       long long N, double tol, CGState *outer, RedWork rw) {
+                       long long N, double tol, int count, CGState *outer, RedWork rw) {
   const int b = blockIdx.y;
   const double *Fb = F + static_cast<size_t>(b) * N, *Ab = Au + static_cast<size_t>(b) * N;
   double *rb = r64 + static_cast<size_t>(b) * N;
@@ -357,7 +360,7 @@ __global__ void __launch_bounds__(kThreads)
     CGState &s = outer[b];
     s.true_rr = tot[0];
     if (!s.active) return;
-    s.iters += 1;
+    s.iters += count;
     s.rr = tot[0];
     s.rel_res = sqrt(tot[0] / s.nF2);
     if (!isfinite(tot[0])) {
@@ -366,6 +369,37 @@ __global__ void __launch_bounds__(kThreads)
     } else if (s.rel_res <= tol) {
       s.active = 0;
     }
+  }
+}
+
+// r64 = F - 2^k (h + l) for the double-float image h + l of 2^-k A u, in
+// FP64 (the FP32 parts are widened and scaled exactly by integer operations),
+// and its norm; provisional: no convergence test, no status change.
+__global__ void __launch_bounds__(kThreads)
+    ir_residual_df_kernel(const double *__restrict__ F, const dfloat *__restrict__ Au, double *__restrict__ r64,
+                          long long N, CGState *outer, RedWork rw) {
+  const int b = blockIdx.y;
+  const int k = ptx::df_scale_exp(outer[b].nF2);
+  const double *Fb = F + static_cast<size_t>(b) * N;
+  const dfloat *Ab = Au + static_cast<size_t>(b) * N;
+  double *rb = r64 + static_cast<size_t>(b) * N;
+  double v[1] = {0.0};
+  for (long long i = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x; i < N;
+       i += static_cast<long long>(gridDim.x) * kThreads) {
+    const dfloat a = Ab[i];
+    const double e = (Fb[i] - ptx::scale_f64(ptx::f32_to_f64(a.h), k)) - ptx::scale_f64(ptx::f32_to_f64(a.l), k);
+    rb[i] = e;
+    v[0] = fma(e, e, v[0]);
+  }
+  double tot[1];
+  if (grid_sum<1>(v, rw, b, tot) && threadIdx.x == 0) {
+    CGState &s = outer[b];
+    s.true_rr = tot[0];
+    if (!s.active) return;
+    s.iters += 1;
+    s.df_iters += 1;
+    s.rr = tot[0];
+    s.rel_res = sqrt(tot[0] / s.nF2);
   }
 }
 
@@ -471,8 +505,13 @@ cudaError_t launch_ir_correct(double *u, const float *d, long long N, int B, con
   return cudaGetLastError();
 }
 cudaError_t launch_ir_residual(const double *F, const double *Au, double *r64, long long N, int B, double tol,
-                               CGState *outer, RedWork rw, cudaStream_t s) {
-  ir_residual_kernel<<<dim3(rw.grid, B), kThreads, 0, s>>>(F, Au, r64, N, tol, outer, rw);
+                               int count, CGState *outer, RedWork rw, cudaStream_t s) {
+  ir_residual_kernel<<<dim3(rw.grid, B), kThreads, 0, s>>>(F, Au, r64, N, tol, count, outer, rw);
+  return cudaGetLastError();
+}
+cudaError_t launch_ir_residual_df(const double *F, const dfloat *Au, double *r64, long long N, int B,
+                                  CGState *outer, RedWork rw, cudaStream_t s) {
+  ir_residual_df_kernel<<<dim3(rw.grid, B), kThreads, 0, s>>>(F, Au, r64, N, outer, rw);
   return cudaGetLastError();
 }
 cudaError_t launch_true_residual(const double *F, const double *Ax, long long N, int B, CGState *st,

@@ -19,6 +19,17 @@ struct ModeView {
   long long out_outer_stride;
 };
 
+// Double-float number: the unevaluated sum h + l of two FP32 values with
+// |l| <= ulp(h) / 2 (Dekker 1971), about 48 significant bits.  Products and
+// sums of such pairs run on the FP32 pipe, 64 times the FP64 rate on GB300.
+struct CGState;
+
+struct alignas(8) dfloat {
+  float h, l;
+  dfloat() = default;
+  __host__ __device__ constexpr explicit dfloat(float v) : h(v), l(0.f) {}
+};
+
 // ---- fused A x for two and three spatial directions (k_apply_a.cu) -------------------
 // Band rows are padded to band_row_stride(p, sizeof(T)) elements (whole 16-byte
 // vectors); b2K holds 2 K exactly.
@@ -71,8 +82,18 @@ struct FusedA {
 template <typename T>
 void toeplitz_rows(const T *const *bands, int nbands, int n, int stride, int *lo, int *hi);
 // y = A x; 2 launches (d = 2) or 3 (d = 3).  x, y: B * N values, colexicographic.
+// T = double, float or dfloat (double-float arithmetic with FP32 operations).
 template <typename T>
 cudaError_t launch_fused_A(const FusedA<T> &f, const T *x, T *y, cudaStream_t s);
+// Double-float images of B vectors of N FP64 values and back: y = x * 2^-k_b
+// split into h + l, and x = 2^k_b (h + l) rounded to FP64, with k_b = 0 when
+// `scale` is NULL, else the exponent of ||F_b|| (frexp of sqrt(scale[b].nF2)),
+// so that the FP32 parts of a solution u stay far from FP32 overflow and
+// underflow.
+cudaError_t launch_df_split(const double *x, dfloat *y, long long N, int B, const CGState *scale,
+                            cudaStream_t s);
+cudaError_t launch_df_join(const dfloat *y, double *x, long long N, int B, const CGState *scale,
+                           cudaStream_t s);
 
 // ---- dense mode product: out = in x_k W (Algorithm 1, steps 2 and 4) -----------------
 // out(o, i, c) = sum_j W[i * n + j] in(o, j, c).  If lam_row != nullptr the
@@ -110,7 +131,7 @@ inline cudaError_t launch_banded_f64(const BandSpec &spec, const ModeView &v, cu
 // ---- CG vector kernels with deterministic grid reductions --------------------------
 struct CGState {
   double rz, pq, alpha, beta, rr, nF2, rel_res, true_rr;
-  int active, iters, status, pad;
+  int active, iters, status, df_iters;  // df_iters: provisional double-float residuals
 };
 struct RedWork {
   double *partials;    // [batch][grid][2]
@@ -139,8 +160,17 @@ cudaError_t launch_cg_p(const T *z, T *p, long long N, int B, int first, CGState
 cudaError_t launch_ir_start(const double *r64, float *r32, float *d, long long N, int B, const CGState *outer,
                             CGState *inner, RedWork rw, cudaStream_t s);
 cudaError_t launch_ir_correct(double *u, const float *d, long long N, int B, const CGState *outer, cudaStream_t s);
+// `count` = 1 when the residual ends an outer step, 0 when it re-evaluates the
+// last one in FP64.
 cudaError_t launch_ir_residual(const double *F, const double *Au, double *r64, long long N, int B, double tol,
-                               CGState *outer, RedWork rw, cudaStream_t s);
+                               int count, CGState *outer, RedWork rw, cudaStream_t s);
+// Same with A u given as the double-float image 2^-k_b A u (launch_df_split's
+// scale taken from `outer`).  The result is provisional: it updates the
+// residual, its norm and the outer step count but never ends a solve or flags
+// a non-finite value; the host confirms convergence (or a non-finite norm)
+// with the FP64 residual.
+cudaError_t launch_ir_residual_df(const double *F, const dfloat *Au, double *r64, long long N, int B,
+                                  CGState *outer, RedWork rw, cudaStream_t s);
 cudaError_t launch_true_residual(const double *F, const double *Ax, long long N, int B, CGState *st,
                                  RedWork rw, cudaStream_t s);
 

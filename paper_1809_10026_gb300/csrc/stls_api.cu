@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "kernels.h"
@@ -45,6 +46,8 @@ struct stls_ctx {
   // device factors
   AOps<double> a64;                 // FP64 A x (residuals, strict forms)
   AOps<float> a32;                  // FP32 A x (inner solves of the refinement form)
+  AOps<stls::dfloat> adf;           // double-float A x (provisional outer residuals)
+  bool have_df = false;
   double *Uf[4] = {}, *Ub[4] = {};  // U^T (forward) and U (backward), row-major
   double *lam_t = nullptr, *lam_s = nullptr;
   double *e_end = nullptr, *m_int = nullptr;
@@ -113,13 +116,27 @@ int upload(stls_ctx *c, T **ptr, const std::vector<T> &h) {
   return STLS_OK;
 }
 
+// FP64 value in the element type: rounded to nearest for float, split into
+// h = fl32(v), l = fl32(v - h) for double-float.
+template <typename T>
+T to_elem(double v) {
+  if constexpr (std::is_same_v<T, stls::dfloat>) {
+    stls::dfloat r;
+    r.h = static_cast<float>(v);
+    r.l = static_cast<float>(v - static_cast<double>(r.h));
+    return r;
+  } else {
+    return static_cast<T>(v);
+  }
+}
+
 // Band rows (2p+1 values) copied into rows of `stride` values, scaled by `scale`.
 template <typename T>
 std::vector<T> pad_band(const std::vector<double> &band, int n, int p, int stride, double scale) {
   const int w = 2 * p + 1;
   std::vector<T> out(static_cast<size_t>(n) * stride, T(0));
   for (int i = 0; i < n; ++i)
-    for (int o = 0; o < w; ++o) out[static_cast<size_t>(i) * stride + o] = static_cast<T>(scale * band[i * w + o]);
+    for (int o = 0; o < w; ++o) out[static_cast<size_t>(i) * stride + o] = to_elem<T>(scale * band[i * w + o]);
   return out;
 }
 
@@ -297,31 +314,47 @@ int spatial_tree(stls_ctx *c, AOps<T> &A, const T *X, long long outer_mult, T *M
 }
 
 template <typename T>
+stls::FusedA<T> fused_args(const stls_ctx *c, const AOps<T> &A) {
+  stls::FusedA<T> f{};
+  f.d = c->d;
+  f.p_s = c->hs.prm.p_s;
+  f.p_t = c->hs.prm.p_t;
+  for (int k = 0; k < c->d; ++k) {
+    f.n[k] = c->n_s[k];
+    f.bM[k] = A.pad_M[k];
+    f.bJ[k] = A.pad_J[k];
+    f.bK[k] = A.pad_K[k];
+    f.b2K[k] = A.pad_2K[k];
+  }
+  f.n_t = c->n_t;
+  f.B = c->B;
+  f.bKt = A.pad_Kt;
+  f.bMt = A.pad_Mt;
+  for (int k = 0; k < 3; ++k) {
+    f.lo[k] = A.lo[k];
+    f.hi[k] = A.hi[k];
+  }
+  f.lo_t = A.lo_t;
+  f.hi_t = A.hi_t;
+  for (int w = 0; w < 5; ++w) f.work[w] = A.abuf[w];
+  f.ls_last = A.ls_buf;
+  return f;
+}
+
+// y = A x in double-float arithmetic (refinement contexts with the fused A x):
+// x, y are double-float images; the work buffers are those of the FP64 A x.
+int apply_A_df_impl(stls_ctx *c, const stls::dfloat *x, stls::dfloat *y) {
+  if (!c->have_df) return set_err(c, STLS_EINVAL, "double-float A x needs a refinement context with d = 2 or 3");
+  const stls::FusedA<stls::dfloat> f = fused_args(c, c->adf);
+  c->launches += c->d - 1;
+  STLS_LAUNCH(stls::launch_fused_A<stls::dfloat>(f, x, y, c->stream), "fused A x (double-float)");
+  return STLS_OK;
+}
+
+template <typename T>
 int apply_A_impl(stls_ctx *c, AOps<T> &A, const T *x, T *y) {
   if (stls::fused_A_supported(c->d, c->hs.prm.p_s, c->hs.prm.p_t)) {
-    stls::FusedA<T> f{};
-    f.d = c->d;
-    f.p_s = c->hs.prm.p_s;
-    f.p_t = c->hs.prm.p_t;
-    for (int k = 0; k < c->d; ++k) {
-      f.n[k] = c->n_s[k];
-      f.bM[k] = A.pad_M[k];
-      f.bJ[k] = A.pad_J[k];
-      f.bK[k] = A.pad_K[k];
-      f.b2K[k] = A.pad_2K[k];
-    }
-    f.n_t = c->n_t;
-    f.B = c->B;
-    f.bKt = A.pad_Kt;
-    f.bMt = A.pad_Mt;
-    for (int k = 0; k < 3; ++k) {
-      f.lo[k] = A.lo[k];
-      f.hi[k] = A.hi[k];
-    }
-    f.lo_t = A.lo_t;
-    f.hi_t = A.hi_t;
-    for (int w = 0; w < 5; ++w) f.work[w] = A.abuf[w];
-    f.ls_last = A.ls_buf;
+    const stls::FusedA<T> f = fused_args(c, A);
     c->launches += c->d - 1;  // d launches in all
     STLS_LAUNCH(stls::launch_fused_A<T>(f, x, y, c->stream), "fused A x");
     return STLS_OK;
@@ -455,6 +488,7 @@ int solve_impl(stls_ctx *c, const double *F, double *u, double tol, int maxit, s
       info[b].rel_res = s.rel_res;
       info[b].true_rel_res = s.nF2 > 0 ? std::sqrt(s.true_rr / s.nF2) : 0.0;
       info[b].outer = 0;
+      info[b].outer_df = 0;
     }
     if (status != STLS_OK && first_bad == STLS_OK) first_bad = status;
   }
@@ -490,12 +524,47 @@ int solve_ir_impl(stls_ctx *c, const double *F, double *u, double tol, int maxit
   int ph = phase_begin(c, 2);
   STLS_LAUNCH(stls::launch_cg_init(F, u, r64, N, B, c->st, c->rw, c->stream), "cg_init");
   phase_end(c, ph);
-  std::vector<CGState> inner_host(B);
-  int total_inner = 0, outer = 0, rc = STLS_OK;
-  for (; outer < kMaxOuter; ++outer) {
+  // Provisional residuals: an outer step whose predicted residual is far
+  // above both tol and the accuracy of double-float arithmetic takes F - A u
+  // with the double-float A x (FP32 operations only); the FP64 residual
+  // confirms every convergence test, a non-finite norm and the last step.
+  // The prediction is ||r|| max(inner residual reached, 4e-4).
+  const double kDfMargin = 100.0, kDfFloor = 1e-8, kContractFloor = 4e-4;
+  double *xdf_buf = c->p;  // FP64 CG vectors, unused by the refinement form
+  auto fp64_residual = [&](int count) -> int {
+    int ph2 = phase_begin(c, 0);
+    int rc2 = apply_A_impl<double>(c, c->a64, u, q64);
+    if (rc2) return rc2;
+    phase_end(c, ph2);
+    ph2 = phase_begin(c, 2);
+    STLS_LAUNCH(stls::launch_ir_residual(F, q64, r64, N, B, tol, count, c->st, c->rw, c->stream), "ir_residual");
+    phase_end(c, ph2);
+    return STLS_OK;
+  };
+  auto read_state = [&]() -> int {
     STLS_CK(cudaMemcpyAsync(c->st_host, c->st, sizeof(CGState) * B, cudaMemcpyDeviceToHost, c->stream),
             "state copy");
     STLS_CK(cudaStreamSynchronize(c->stream), "sync");
+    return STLS_OK;
+  };
+  std::vector<CGState> inner_host(B);
+  int total_inner = 0, outer = 0, rc = STLS_OK;
+  bool last_df = false;
+  for (; outer < kMaxOuter; ++outer) {
+    rc = read_state();
+    if (rc) return rc;
+    if (last_df) {
+      bool confirm = total_inner >= maxit || outer + 1 >= kMaxOuter;
+      for (int b = 0; b < B; ++b)
+        if (c->st_host[b].active && !(c->st_host[b].rel_res > tol && std::isfinite(c->st_host[b].rel_res)))
+          confirm = true;
+      if (confirm) {
+        rc = fp64_residual(0);
+        if (!rc) rc = read_state();
+        if (rc) return rc;
+        last_df = false;
+      }
+    }
     bool any = false;
     double worst = 0.0;
     for (int b = 0; b < B; ++b)
@@ -558,19 +627,37 @@ int solve_ir_impl(stls_ctx *c, const double *F, double *u, double tol, int maxit
       phase_end(c, ph);
     }
     int its = 0;
-    for (int b = 0; b < B; ++b) its = std::max(its, inner_host[b].iters);
+    double inner_worst = 0.0;
+    for (int b = 0; b < B; ++b) {
+      its = std::max(its, inner_host[b].iters);
+      if (c->st_host[b].active) inner_worst = std::max(inner_worst, inner_host[b].rel_res);
+    }
     total_inner += std::max(its, 1);
     // ---- FP64 correction and residual ----
     ph = phase_begin(c, 2);
     STLS_LAUNCH(stls::launch_ir_correct(u, c->di, N, B, c->st, c->stream), "ir_correct");
     phase_end(c, ph);
-    ph = phase_begin(c, 0);
-    rc = apply_A_impl<double>(c, c->a64, u, q64);
+    const double predicted = worst * std::max(inner_worst, kContractFloor);
+    if (c->have_df && predicted > kDfMargin * tol && predicted > kDfFloor && total_inner < maxit) {
+      stls::dfloat *xdf = reinterpret_cast<stls::dfloat *>(xdf_buf), *ydf = reinterpret_cast<stls::dfloat *>(q64);
+      ph = phase_begin(c, 0);
+      STLS_LAUNCH(stls::launch_df_split(u, xdf, N, B, c->st, c->stream), "df_split");
+      rc = apply_A_df_impl(c, xdf, ydf);
+      if (rc) return rc;
+      phase_end(c, ph);
+      ph = phase_begin(c, 2);
+      STLS_LAUNCH(stls::launch_ir_residual_df(F, ydf, r64, N, B, c->st, c->rw, c->stream), "ir_residual_df");
+      phase_end(c, ph);
+      last_df = true;
+    } else {
+      rc = fp64_residual(1);
+      if (rc) return rc;
+      last_df = false;
+    }
+  }
+  if (last_df) {  // the outer step limit ended the loop after a provisional residual
+    rc = fp64_residual(0);
     if (rc) return rc;
-    phase_end(c, ph);
-    ph = phase_begin(c, 2);
-    STLS_LAUNCH(stls::launch_ir_residual(F, q64, r64, N, B, tol, c->st, c->rw, c->stream), "ir_residual");
-    phase_end(c, ph);
   }
   STLS_CK(cudaMemcpyAsync(c->st_host, c->st, sizeof(CGState) * B, cudaMemcpyDeviceToHost, c->stream),
           "state copy");
@@ -587,6 +674,7 @@ int solve_ir_impl(stls_ctx *c, const double *F, double *u, double tol, int maxit
       info[b].rel_res = s.rel_res;
       info[b].true_rel_res = s.nF2 > 0 ? std::sqrt(s.rr / s.nF2) : 0.0;
       info[b].outer = s.iters;
+      info[b].outer_df = s.df_iters;
     }
     if (status != STLS_OK && first_bad == STLS_OK) first_bad = status;
   }
@@ -654,6 +742,9 @@ int stls_create(stls_ctx **out, const stls_params *prm, void *cuda_stream) {
   };
   int rc = STLS_OK;
   const bool refine = P.refine != 0;
+  // double-float A x for the provisional outer residuals of the refinement form
+  const bool df = refine && stls::fused_A_supported(c->d, P.p_s, P.p_t);
+  c->have_df = df;
   auto to_f32 = [](const std::vector<double> &v) { return std::vector<float>(v.begin(), v.end()); };
   for (int k = 0; k < c->d && !rc; ++k) {
     const stls::Dir1D &D = c->hs.space[k];
@@ -667,6 +758,7 @@ int stls_create(stls_ctx **out, const stls_params *prm, void *cuda_stream) {
     if (!rc && refine) rc = upload(c, &c->a32.band_J[k], to_f32(bJ));
     if (!rc) rc = upload_padded(c, c->a64, k, D, bM, bK, bJ);
     if (!rc && refine) rc = upload_padded(c, c->a32, k, D, bM, bK, bJ);
+    if (!rc && df) rc = upload_padded(c, c->adf, k, D, bM, bK, bJ);
     if (!rc) rc = upload(c, &c->Uf[k], transpose(c->hs.eig_s[k].U, D.n));
     if (!rc) rc = upload(c, &c->Ub[k], c->hs.eig_s[k].U);
   }
@@ -679,6 +771,7 @@ int stls_create(stls_ctx **out, const stls_params *prm, void *cuda_stream) {
     if (!rc && refine) rc = upload(c, &c->a32.band_Mt, to_f32(bMt));
     if (!rc) rc = upload_padded_time(c, c->a64, Tm, bKt, bMt);
     if (!rc && refine) rc = upload_padded_time(c, c->a32, Tm, bKt, bMt);
+    if (!rc && df) rc = upload_padded_time(c, c->adf, Tm, bKt, bMt);
   }
   if (!rc) rc = upload(c, &c->Uf[c->d], transpose(c->hs.eig_t.U, Tm.n));
   if (!rc) rc = upload(c, &c->Ub[c->d], c->hs.eig_t.U);
@@ -706,6 +799,10 @@ int stls_create(stls_ctx **out, const stls_params *prm, void *cuda_stream) {
     if (!rc) rc = dev_alloc(c, v, BN);
   for (int a = 0; a < 8 && !rc; ++a) rc = dev_alloc(c, &c->a64.abuf[a], BN);
   if (!rc) rc = dev_alloc(c, &c->a64.ls_buf, BNs);
+  if (df) {  // the double-float A x shares the FP64 A x buffers (same element size)
+    for (int a = 0; a < 8; ++a) c->adf.abuf[a] = reinterpret_cast<stls::dfloat *>(c->a64.abuf[a]);
+    c->adf.ls_buf = reinterpret_cast<stls::dfloat *>(c->a64.ls_buf);
+  }
   if (refine) {
     for (int a = 0; a < 8 && !rc; ++a) rc = dev_alloc(c, &c->a32.abuf[a], BN);
     if (!rc) rc = dev_alloc(c, &c->a32.ls_buf, BNs);
@@ -779,6 +876,19 @@ int stls_apply_A(stls_ctx *c, const double *x, double *y) {
   if (check_ptr(c, x, "x") || check_ptr(c, y, "y")) return STLS_EINVAL;
   if (x == y) return set_err(c, STLS_EINVAL, "apply_A: x and y must not overlap");
   return apply_A_impl<double>(c, c->a64, x, y);
+}
+
+int stls_apply_A_df(stls_ctx *c, const double *x, double *y) {
+  if (c == nullptr) return STLS_EINVAL;
+  if (check_ptr(c, x, "x") || check_ptr(c, y, "y")) return STLS_EINVAL;
+  if (x == y) return set_err(c, STLS_EINVAL, "apply_A_df: x and y must not overlap");
+  if (!c->have_df) return set_err(c, STLS_EINVAL, "apply_A_df needs a refinement context with d = 2 or 3");
+  stls::dfloat *xd = reinterpret_cast<stls::dfloat *>(c->p), *yd = reinterpret_cast<stls::dfloat *>(c->z);
+  STLS_LAUNCH(stls::launch_df_split(x, xd, c->N, c->B, nullptr, c->stream), "df_split");
+  int rc = apply_A_df_impl(c, xd, yd);
+  if (rc) return rc;
+  STLS_LAUNCH(stls::launch_df_join(yd, y, c->N, c->B, nullptr, c->stream), "df_join");
+  return STLS_OK;
 }
 
 int stls_apply_precond(stls_ctx *c, const double *r, double *z) {

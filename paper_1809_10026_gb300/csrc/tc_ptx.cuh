@@ -220,8 +220,8 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 
 // Hardware conversions for the rare inputs of the integer paths below, kept
 // out of line so that the common path issues no FP64-pipe instruction.
-__device__ __noinline__ float f64_to_f32_hw(double x) { return __double2float_rn(x); }
-__device__ __noinline__ double f32_to_f64_hw(float f) { return static_cast<double>(f); }
+static __device__ __noinline__ float f64_to_f32_hw(double x) { return __double2float_rn(x); }
+static __device__ __noinline__ double f32_to_f64_hw(float f) { return static_cast<double>(f); }
 
 // Integer part of f64_to_f32_rn for results in the FP32 normal range and
 // zeros; `ok` is cleared for any other input (then the value is not used).
@@ -284,6 +284,29 @@ __device__ __forceinline__ double f32_to_f64(float f) {
   }
   if ((b & 0x7FFFFFFFu) == 0u) return __hiloint2double(static_cast<int>(b & 0x80000000u), 0);
   return f32_to_f64_hw(f);
+}
+
+// x * 2^s for FP64 x: an integer add to the exponent field when x and the
+// result are normal numbers; zeros unchanged; anything else (subnormal,
+// infinite, NaN, or a result out of the normal range) by the hardware ldexp.
+static __device__ __noinline__ double scale_f64_hw(double x, int s) { return ldexp(x, s); }
+__device__ __forceinline__ double scale_f64(double x, int s) {
+  const long long u = __double_as_longlong(x);
+  const int e = static_cast<int>((u >> 52) & 0x7FF);
+  if (e >= 1 && e <= 2046 && e + s >= 1 && e + s <= 2046)
+    return __longlong_as_double(u + (static_cast<long long>(s) << 52));
+  if ((u & 0x7FFFFFFFFFFFFFFFLL) == 0) return x;
+  return scale_f64_hw(x, s);
+}
+
+// Binary exponent k of ||F|| (||F|| = f 2^k, f in [0.5, 1)); 0 for a zero or
+// non-finite norm.  Double-float images of solution-sized vectors are scaled
+// by 2^-k.
+__device__ __forceinline__ int df_scale_exp(double nF2) {
+  const double nf = sqrt(nF2);
+  int k = 0;
+  if (nf > 0.0 && isfinite(nf)) frexp(nf, &k);
+  return k;
 }
 
 // Instruction descriptor of kind::f16 with BF16 A and B, FP32 D, shape M x N;

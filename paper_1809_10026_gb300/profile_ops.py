@@ -17,7 +17,7 @@ from paper_1809_10026_gb300 import synth
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--op", choices=["precond", "apply_A", "solve"], default="precond")
+    ap.add_argument("--op", choices=["precond", "apply_A", "apply_A_df", "solve"], default="precond")
     ap.add_argument("--precision", choices=["fp64", "tf32", "bf16"], default="fp64")
     ap.add_argument("--d", type=int, default=3)
     ap.add_argument("--p", type=int, default=3)
@@ -39,6 +39,8 @@ def main():
             S.apply_precond(x, out=y)
         elif a.op == "apply_A":
             S.apply_A(x, out=y)
+        elif a.op == "apply_A_df":
+            S.apply_A_df(x, out=y)
         else:
             S.solve(x, a.tol, 500, out=y)
 

@@ -166,10 +166,14 @@ def test_refinement_solve_cfg3(form):
     S = _solver(3, 4, 32, precision=form, refine=True)
     u8, i8 = S.solve(Fg, tol=1e-8, maxit=400)
     assert i8[0]["status"] == "ok" and i8[0]["true_rel_res"] <= 1e-8 and i8[0]["outer"] >= 2
+    # the first outer step's residual (predicted ~1e-3) is a provisional double-float one
+    assert 1 <= i8[0]["outer_df"] < i8[0]["outer"]
     u12, i12 = S.solve(Fg, tol=1e-12, maxit=800)
     assert i12[0]["status"] == "ok" and i12[0]["true_rel_res"] <= 1e-12
     assert _rel(u12.cpu().numpy(), u64.cpu().numpy()) <= 1e-8
-    print(form, "refine: inner", i8[0]["iters"], "outer", i8[0]["outer"], "| 1e-12:", i12[0]["iters"], i12[0]["outer"])
+    assert i12[0]["outer_df"] < i12[0]["outer"]
+    print(form, "refine: inner", i8[0]["iters"], "outer", i8[0]["outer"], "df", i8[0]["outer_df"],
+          "| 1e-12:", i12[0]["iters"], i12[0]["outer"], i12[0]["outer_df"])
 
 
 def test_refinement_batch_matches_direct_solve():
