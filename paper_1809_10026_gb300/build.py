@@ -13,7 +13,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libstls.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["host_setup.cpp", "stls_api.cu", "k_modeprod_f64.cu", "k_banded_f64.cu", "k_cg.cu",
-           "tc_fd.cu", "tc_fd_fused.cu", "fd_noalloc.cu",
+           "tc_fd.cu", "tc_fd_fused.cu", "tc_fd_tf32.cu", "fd_noalloc.cu",
            "k_apply_a.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",

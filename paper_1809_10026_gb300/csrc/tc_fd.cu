@@ -438,6 +438,19 @@ cudaError_t tc_fd_create(TcFd &tc, int precision, int d, const int *n, int B,
     if (e == cudaSuccess && err.empty()) tc.launches_per_apply = tc_fd_fused_launches(tc.fused);
     return e;
   }
+  if (tc_fd_rot_eligible(precision, d, n, B)) {
+    std::string rerr;
+    e = tc_fd_rot_create(tc.rot, tc.allocations, d, n, B, U, lam, im->err_dev, rerr);
+    if (e == cudaSuccess && rerr.empty()) {
+      tc.launches_per_apply = tc_fd_rot_launches(tc.rot);
+      return e;
+    }
+    // a tensor map or pipeline the sizes do not allow: per-mode kernels below
+    tc_fd_rot_destroy(tc.rot);
+    tc.rot = nullptr;
+    if (e != cudaSuccess && e != cudaErrorInvalidConfiguration) return e;
+    cudaGetLastError();
+  }
   for (int k = 0; k <= d; ++k) {
     Mode &m = im->mode[k];
     m.n = n[k];
@@ -540,11 +553,13 @@ cudaError_t apply_passes(TcFd &tc, const IO *r, IO *z, cudaStream_t s) {
 
 cudaError_t tc_fd_apply(TcFd &tc, const double *r, double *z, cudaStream_t s) {
   if (tc.fused != nullptr) return tc_fd_fused_apply<double>(tc.fused, r, z, s);
+  if (tc.rot != nullptr) return tc_fd_rot_apply<double>(tc.rot, r, z, s);
   return apply_passes<double>(tc, r, z, s);
 }
 
 cudaError_t tc_fd_apply_f32(TcFd &tc, const float *r, float *z, cudaStream_t s) {
   if (tc.fused != nullptr) return tc_fd_fused_apply<float>(tc.fused, r, z, s);
+  if (tc.rot != nullptr) return tc_fd_rot_apply<float>(tc.rot, r, z, s);
   return apply_passes<float>(tc, r, z, s);
 }
 
@@ -558,6 +573,8 @@ int tc_fd_launch_count(const TcFd &tc) { return tc.launches_per_apply; }
 void tc_fd_destroy(TcFd &tc) {
   if (tc.fused != nullptr) tc_fd_fused_destroy(tc.fused);
   tc.fused = nullptr;
+  if (tc.rot != nullptr) tc_fd_rot_destroy(tc.rot);
+  tc.rot = nullptr;
   for (void *p : tc.allocations) cudaFree(p);
   tc.allocations.clear();
   Impl *im = static_cast<Impl *>(tc.impl);

@@ -12,6 +12,7 @@
 namespace stls {
 
 struct FusedFd;
+struct RotFd;
 
 struct TcFd {
   int precision = 0, d = 0, B = 0;
@@ -21,6 +22,7 @@ struct TcFd {
   std::vector<void *> allocations;
   void *impl = nullptr;
   FusedFd *fused = nullptr;  // BF16, d = 2, 3: fused passes (tc_fd_fused.cu)
+  RotFd *rot = nullptr;      // TF32: TMA-fed rotation passes (tc_fd_tf32.cu)
 };
 
 // U[k] (row-major n[k] x n[k], k = 0..d-1 space, d = time) are the FP64
@@ -49,6 +51,16 @@ template <typename IO>
 cudaError_t tc_fd_fused_apply(FusedFd *f, const IO *r, IO *z, cudaStream_t s);
 int tc_fd_fused_launches(const FusedFd *f);
 void tc_fd_fused_destroy(FusedFd *f);
+// TF32 rotation passes (tc_fd_tf32.cu): 2(d+1) mode products with TMA-fed
+// K-major operands and a padding pass for r.
+bool tc_fd_rot_eligible(int precision, int d, const int *n, int B);
+cudaError_t tc_fd_rot_create(RotFd *&out, std::vector<void *> &allocs, int d, const int *n, int B,
+                             const std::vector<std::vector<double>> &U, const std::vector<std::vector<double>> &lam,
+                             int *err_dev, std::string &err);
+template <typename IO>
+cudaError_t tc_fd_rot_apply(RotFd *f, const IO *r, IO *z, cudaStream_t s);
+int tc_fd_rot_launches(const RotFd *f);
+void tc_fd_rot_destroy(RotFd *f);
 // y = FP64(BF16(FP32(x))), both roundings to nearest even, as the fused kernels round r.
 cudaError_t round_bf16_launch(const double *x, double *y, long long n, cudaStream_t s);
 

@@ -45,6 +45,16 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
 
+// D[tmem] (+)= A * B, TF32 operands (the top 19 bits of each FP32 operand),
+// FP32 accumulator, issued by one thread.
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
 // Arrive on `mbar` once every MMA issued so far by this thread has completed.
 __device__ __forceinline__ void mma_commit(uint32_t mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
@@ -203,6 +213,15 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map
       : "memory");
 }
 
+// Tiled tensor (TMA) load of one box of a 2D tensor at coordinates (c0, c1).
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int c0, int c1, uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+      "[%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(mbar)
+      : "memory");
+}
+
 // Tiled tensor (TMA) store of one box from shared memory, in the current bulk group.
 __device__ __forceinline__ void tma_store_3d(const CUtensorMap *map, int c0, int c1, int c2, uint32_t src) {
   asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
@@ -320,6 +339,25 @@ __host__ __device__ inline uint32_t idesc_bf16(int M, int N, int b_mn_major) {
   d |= static_cast<uint32_t>(N >> 3) << 17;
   d |= static_cast<uint32_t>(M >> 4) << 24;
   return d;
+}
+
+// Instruction descriptor of kind::tf32 with TF32 A and B (both K-major), FP32 D.
+__host__ __device__ inline uint32_t idesc_tf32(int M, int N) {
+  uint32_t d = 0;
+  d |= 1u << 4;   // D format F32
+  d |= 2u << 7;   // A format TF32
+  d |= 2u << 10;  // B format TF32
+  d |= static_cast<uint32_t>(N >> 3) << 17;
+  d |= static_cast<uint32_t>(M >> 4) << 24;
+  return d;
+}
+
+// FP32 -> TF32, round to nearest with ties away from zero (cvt.rna), as an
+// FP32 value whose low 13 significand bits are zero.
+__device__ __forceinline__ float tf32_rna(float v) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+  return __uint_as_float(r);
 }
 
 }  // namespace ptx
