@@ -7,15 +7,17 @@ One step = one complete solve A u = F from u = 0 to ||r|| / ||F|| <= 1e-8
 direction, N = 18,125,250 unknowns, F ~ U[-1,1] (seed 1809100264).
 
 Metric: solved degrees of freedom per second (DoF/s), whole job.  The
-headline form is the mixed one of this workload: BF16 tensor-core
+headline form is the mixed one of this workload: TF32 tensor-core
 preconditioner apply with FP32 accumulation, FP64 outer residual F - A u
 (iterative refinement around a flexible CG in FP32 with FP64-accumulated inner
-products).  The other forms are measured on the same workload in the same run
-and reported under "forms": TF32 refinement, the strict BF16 form (flexible CG
-with FP64 vectors, FP64 A x, only the preconditioner in BF16) and the FP64 PCG.
+products; the outer steps before the last take a provisional residual with
+the double-float A x).  The other forms are measured on the same workload in
+the same run and reported under "forms": BF16 refinement, the strict BF16
+form (flexible CG with FP64 vectors, FP64 A x, only the preconditioner in
+BF16) and the FP64 PCG.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--precision bf16|tf32|fp64] [--no-refine] [--forms a,b,...]
+                  [--precision tf32|bf16|fp64] [--no-refine] [--forms a,b,...]
 
 With --gpus N > 1 (under torchrun) every rank solves its own copy of the
 workload (replicas; the method has no data-path exchange on one node) and
@@ -221,6 +223,13 @@ def roofline_entry(phase, ms, count, S, p, peaks, refine):
         e = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
              "kernel": "A x, FP32 fused banded mode products",
              "peak_source": "FP32 FMA units x max SM clock (152 x 128 x 2 x 2.07 GHz)"}
+    elif phase == "apply_A_df":
+        # 12 FP32 operations per banded term (an FMA counts as one operation)
+        ops = 12 * apply_A_flops(S, p) / 2
+        ach = ops / per / 1e12
+        e = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS / 2, "unit": "Top/s",
+             "kernel": "A x, double-float fused banded mode products (with the split of u)",
+             "peak_source": "FP32 operations: 152 SMs x 128 lanes x 2.07 GHz"}
     else:
         return None
     e["frac"] = e["achieved"] / e["peak"]
@@ -445,10 +454,10 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp64", "tf32", "bf16"], default="bf16")
+    ap.add_argument("--precision", choices=["fp64", "tf32", "bf16"], default="tf32")
     ap.add_argument("--no-refine", action="store_true",
                     help="headline mixed form without the FP64 outer residual (strict flexible CG)")
-    ap.add_argument("--forms", default="tf32_ir,bf16_fcg,fp64_pcg",
+    ap.add_argument("--forms", default="bf16_ir,bf16_fcg,fp64_pcg",
                     help="other forms timed in the same run (comma separated; empty for none)")
     ap.add_argument("--form-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -202,6 +202,10 @@ long long stls_launch_count(const stls_ctx *ctx);
  * of executions since the last reset (arrays of 4). */
 int stls_enable_timing(stls_ctx *ctx, int on);
 int stls_phase_times(stls_ctx *ctx, double *ms_out4, long long *count_out4);
+/* As stls_phase_times for the first min(n, 5) phase ids, adding
+ * 4 = A x in double-float arithmetic (the refinement form's provisional
+ * residuals, with the split of u).  ms_out, count_out: n entries or NULL. */
+int stls_phase_times_n(stls_ctx *ctx, int n, double *ms_out, long long *count_out);
 
 /* ---- allocation-free preconditioner apply ------------------------------------
  * The paper has no counterpart to this entry point; it serves callers that

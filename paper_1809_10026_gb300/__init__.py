@@ -197,11 +197,11 @@ class Solver:
         _check(self.lib.stls_enable_timing(self.ctx, int(on)), self.ctx)
 
     def phase_times(self):
-        ms = (ctypes.c_double * 4)()
-        cnt = (ctypes.c_longlong * 4)()
-        _check(self.lib.stls_phase_times(self.ctx, ms, cnt), self.ctx)
-        names = ["apply_A", "precond", "cg_vectors", "apply_A_f32"]
-        return {names[i]: (ms[i], cnt[i]) for i in range(4)}
+        names = ["apply_A", "precond", "cg_vectors", "apply_A_f32", "apply_A_df"]
+        ms = (ctypes.c_double * len(names))()
+        cnt = (ctypes.c_longlong * len(names))()
+        _check(self.lib.stls_phase_times_n(self.ctx, len(names), ms, cnt), self.ctx)
+        return {names[i]: (ms[i], cnt[i]) for i in range(len(names))}
 
     def close(self):
         if getattr(self, "ctx", None) and self.ctx.value:

@@ -14,7 +14,7 @@ FACTOR = {"mass": 0, "stiff": 1, "bilap": 2, "eigvec": 3, "eigval": 4, "end": 5,
 EXPORTS = ["stls_create", "stls_destroy", "stls_last_error", "stls_set_stream", "stls_sizes",
            "stls_apply_A", "stls_apply_A_df", "stls_apply_precond", "stls_solve", "stls_solve_host", "stls_apply_lift",
            "stls_lift_adjoint", "stls_get_factor", "stls_host_factor", "stls_launch_count",
-           "stls_enable_timing", "stls_phase_times", "stls_apply_precond_noalloc", "stls_round_bf16"]
+           "stls_enable_timing", "stls_phase_times", "stls_phase_times_n", "stls_apply_precond_noalloc", "stls_round_bf16"]
 
 
 class Params(ctypes.Structure):
@@ -70,6 +70,7 @@ def load():
     lib.stls_launch_count.restype = ctypes.c_longlong
     lib.stls_enable_timing.argtypes = [vp, i]
     lib.stls_phase_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
+    lib.stls_phase_times_n.argtypes = [vp, i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
     lib.stls_apply_precond_noalloc.argtypes = [i, ctypes.POINTER(ctypes.c_int), i, ctypes.POINTER(vp),
                                                ctypes.POINTER(vp), vp, vp, vp]
     lib.stls_round_bf16.argtypes = [vp, vp, ctypes.c_longlong, vp]

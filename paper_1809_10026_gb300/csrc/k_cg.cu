@@ -95,7 +95,7 @@ __device__ bool grid_sum(double (&v)[NV], RedWork rw, int b, double (&tot)[NV]) 
   return true;
 }
 
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 8)
     cg_init_kernel(const double *__restrict__ F, double *__restrict__ x, double *__restrict__ r,
                    long long N, CGState *st, RedWork rw) {
   const int b = blockIdx.y;
@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 8)
     cg_alpha_kernel(const T *__restrict__ p, const T *__restrict__ q, long long N,
                     CGState *st, RedWork rw) {
   const int b = blockIdx.y;
@@ -166,10 +166,19 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kThreads)
+// PadOut (FP32 only): also writes r rounded to TF32 into rows of `pad.n`
+// values `pad.np` apart (the TF32 preconditioner's first input), so that the
+// preconditioner needs no padding pass.
+struct PadOut {
+  float *out;
+  int n, np;
+};
+
+// (8 blocks of 256 threads per SM: the reduction grid is sized for that)
+template <typename T, bool PAD = false>
+__global__ void __launch_bounds__(kThreads, 8)
     cg_xr_kernel(T *__restrict__ x, T *__restrict__ r, const T *__restrict__ p,
-                 const T *__restrict__ q, long long N, double tol, CGState *st, RedWork rw) {
+                 const T *__restrict__ q, long long N, double tol, CGState *st, RedWork rw, PadOut pad = {}) {
   const int b = blockIdx.y;
   const bool active = st[b].active != 0;
   const T alpha = static_cast<T>(st[b].alpha);
@@ -179,12 +188,35 @@ __global__ void __launch_bounds__(kThreads)
   if (active) {
     if constexpr (sizeof(T) == 4) {
       Dot2f acc;
-      for (long long i = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x; i < N;
-           i += static_cast<long long>(gridDim.x) * kThreads) {
+      const long long i0 = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x;
+      const long long S = static_cast<long long>(gridDim.x) * kThreads;
+      // offset of entry i in the padded copy (i + (i / n) (np - n)), advanced
+      // without divisions: col = i mod n
+      unsigned off = 0, soff = 0;
+      int col = 0, scol = 0;
+      float *pb_out = nullptr;
+      if (PAD) {
+        const long long row = i0 / pad.n, srow = S / pad.n;
+        col = static_cast<int>(i0 - row * pad.n);
+        scol = static_cast<int>(S - srow * pad.n);
+        off = static_cast<unsigned>(row * pad.np + col);
+        soff = static_cast<unsigned>(srow * pad.np + scol);
+        pb_out = pad.out + static_cast<size_t>(b) * (N / pad.n) * pad.np;
+      }
+      for (long long i = i0; i < N; i += S) {
         xb[i] = fma(alpha, pb[i], xb[i]);
         const T ri = fma(-alpha, qb[i], rb[i]);
         rb[i] = ri;
         acc.add(ri, ri);
+        if (PAD) {
+          pb_out[off] = ptx::tf32_rna(ri);
+          off += soff;
+          col += scol;
+          if (col >= pad.n) {
+            col -= pad.n;
+            off += pad.np - pad.n;
+          }
+        }
       }
       v[0] = acc.value();
     } else {
@@ -214,7 +246,7 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 8)
     cg_beta_kernel(const T *__restrict__ z, const T *__restrict__ r,
                    const T *__restrict__ q, long long N, int flexible, int first, CGState *st,
                    RedWork rw) {
@@ -269,7 +301,7 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 8)
     cg_p_kernel(const T *__restrict__ z, T *__restrict__ p, long long N, int first,
                 const CGState *st) {
   const int b = blockIdx.y;
@@ -282,7 +314,7 @@ __global__ void __launch_bounds__(kThreads)
     pb[i] = first ? zb[i] : fma(beta, pb[i], zb[i]);
 }
 
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 8)
     true_residual_kernel(const double *__restrict__ F, const double *__restrict__ Ax, long long N,
                          CGState *st, RedWork rw) {
   const int b = blockIdx.y;
@@ -297,23 +329,27 @@ __global__ void __launch_bounds__(kThreads)
   if (grid_sum<1>(v, rw, b, tot) && threadIdx.x == 0) st[b].true_rr = tot[0];
 }
 
-// Refinement form: inner right-hand side r32 = r64 / ||r64|| (FP32), d = 0,
-// and the inner CG state for it (active where the outer solve is active).
-__global__ void __launch_bounds__(kThreads)
+// Refinement form: inner right-hand side r32 = r64 2^-k (FP32, rounded to
+// nearest; ||r64|| = f 2^k with f in [0.5, 1), so the power-of-two scaling is
+// exact and done on the exponent field), d = 0, and the inner CG state for it
+// (active where the outer solve is active).  No FP64 arithmetic per entry: the
+// norm is accumulated by Dot2f.
+__global__ void __launch_bounds__(kThreads, 8)
     ir_start_kernel(const double *__restrict__ r64, float *__restrict__ r32, float *__restrict__ d,
                     long long N, const CGState *outer, CGState *inner, RedWork rw) {
   const int b = blockIdx.y;
-  const double scale = outer[b].rr > 0.0 ? 1.0 / sqrt(outer[b].rr) : 0.0;
+  const int k = ptx::df_scale_exp(outer[b].rr);
   const double *rb = r64 + static_cast<size_t>(b) * N;
   float *ib = r32 + static_cast<size_t>(b) * N, *db = d + static_cast<size_t>(b) * N;
-  double v[1] = {0.0};
+  Dot2f acc;
   for (long long i = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x; i < N;
        i += static_cast<long long>(gridDim.x) * kThreads) {
-    const float x = static_cast<float>(rb[i] * scale);
+    const float x = ptx::f64_to_f32_rn(ptx::scale_f64(rb[i], -k));
     ib[i] = x;
     db[i] = 0.f;
-    v[0] = fma(static_cast<double>(x), static_cast<double>(x), v[0]);
+    acc.add(x, x);
   }
+  double v[1] = {acc.value()};
   double tot[1];
   if (grid_sum<1>(v, rw, b, tot) && threadIdx.x == 0) {
     CGState &s = inner[b];
@@ -327,22 +363,40 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
-// u += ||r64|| d for the right-hand sides whose outer solve is active.
-__global__ void __launch_bounds__(kThreads)
-    ir_correct_kernel(double *__restrict__ u, const float *__restrict__ d, long long N, const CGState *outer) {
+// u += 2^k d (the scaling of ir_start undone exactly) for the right-hand sides
+// whose outer solve is active; one FP64 add per entry.  With udf != NULL also
+// the double-float image of the new u (launch_df_split's, scaled by the
+// exponent of ||F||), for every right-hand side.
+__global__ void __launch_bounds__(kThreads, 8)
+    ir_correct_kernel(double *__restrict__ u, const float *__restrict__ d, dfloat *__restrict__ udf, long long N,
+                      const CGState *outer) {
   const int b = blockIdx.y;
-  if (!outer[b].active) return;
-  const double s = sqrt(outer[b].rr);
+  const bool active = outer[b].active != 0;
+  if (!active && udf == nullptr) return;
+  const int k = ptx::df_scale_exp(outer[b].rr), kF = ptx::df_scale_exp(outer[b].nF2);
   double *ub = u + static_cast<size_t>(b) * N;
   const float *db = d + static_cast<size_t>(b) * N;
+  dfloat *yb = udf != nullptr ? udf + static_cast<size_t>(b) * N : nullptr;
   for (long long i = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x; i < N;
-       i += static_cast<long long>(gridDim.x) * kThreads)
-    ub[i] = fma(s, static_cast<double>(db[i]), ub[i]);
+       i += static_cast<long long>(gridDim.x) * kThreads) {
+    double v = ub[i];
+    if (active) {
+      v += ptx::scale_f64(ptx::f32_to_f64(db[i]), k);
+      ub[i] = v;
+    }
+    if (yb != nullptr) {
+      const double w = ptx::scale_f64(v, -kF);
+      dfloat o;
+      o.h = ptx::f64_to_f32_rn(w);
+      o.l = ptx::f64_to_f32_rn(w - ptx::f32_to_f64(o.h));
+      yb[i] = o;
+    }
+  }
 }
 
 // r64 = F - A u in FP64 and the outer convergence test on ||r64|| / ||F||
 // (`count`: whether this residual ends an outer step).
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 8)
     ir_residual_kernel(const double *__restrict__ F, const double *__restrict__ Au, double *__restrict__ r64,
                        long long N, double tol, int count, CGState *outer, RedWork rw) {
   const int b = blockIdx.y;
@@ -375,7 +429,7 @@ __global__ void __launch_bounds__(kThreads)
 // r64 = F - 2^k (h + l) for the double-float image h + l of 2^-k A u, in
 // FP64 (the FP32 parts are widened and scaled exactly by integer operations),
 // and its norm; provisional: no convergence test, no status change.
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 8)
     ir_residual_df_kernel(const double *__restrict__ F, const dfloat *__restrict__ Au, double *__restrict__ r64,
                           long long N, CGState *outer, RedWork rw) {
   const int b = blockIdx.y;
@@ -495,13 +549,22 @@ cudaError_t launch_cg_p(const T *z, T *p, long long N, int B, int first, CGState
 STLS_INST(double)
 STLS_INST(float)
 #undef STLS_INST
+cudaError_t launch_cg_xr_pad(float *x, float *r, const float *p, const float *q, long long N, int B, double tol,
+                             CGState *st, RedWork rw, float *rpad, int n0, int np0, cudaStream_t s) {
+  if (n0 < 1 || np0 < n0 || N % n0 != 0 || static_cast<double>(N / n0) * np0 >= 4294967296.0)
+    return cudaErrorInvalidValue;
+  PadOut pad{rpad, n0, np0};
+  cg_xr_kernel<float, true><<<dim3(rw.grid, B), kThreads, 0, s>>>(x, r, p, q, N, tol, st, rw, pad);
+  return cudaGetLastError();
+}
 cudaError_t launch_ir_start(const double *r64, float *r32, float *d, long long N, int B, const CGState *outer,
                             CGState *inner, RedWork rw, cudaStream_t s) {
   ir_start_kernel<<<dim3(rw.grid, B), kThreads, 0, s>>>(r64, r32, d, N, outer, inner, rw);
   return cudaGetLastError();
 }
-cudaError_t launch_ir_correct(double *u, const float *d, long long N, int B, const CGState *outer, cudaStream_t s) {
-  ir_correct_kernel<<<dim3(grid_1d(N), B), kThreads, 0, s>>>(u, d, N, outer);
+cudaError_t launch_ir_correct(double *u, const float *d, dfloat *udf, long long N, int B, const CGState *outer,
+                              cudaStream_t s) {
+  ir_correct_kernel<<<dim3(grid_1d(N), B), kThreads, 0, s>>>(u, d, udf, N, outer);
   return cudaGetLastError();
 }
 cudaError_t launch_ir_residual(const double *F, const double *Au, double *r64, long long N, int B, double tol,

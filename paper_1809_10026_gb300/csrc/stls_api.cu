@@ -66,8 +66,8 @@ struct stls_ctx {
   std::string err;
   // timing
   bool timing = false;
-  double phase_ms[4] = {0, 0, 0, 0};
-  long long phase_count[4] = {0, 0, 0, 0};
+  double phase_ms[5] = {0, 0, 0, 0, 0};
+  long long phase_count[5] = {0, 0, 0, 0, 0};
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, int>> ev_pairs;  // (phase, first event index)
 };
@@ -550,6 +550,8 @@ int solve_ir_impl(stls_ctx *c, const double *F, double *u, double tol, int maxit
   std::vector<CGState> inner_host(B);
   int total_inner = 0, outer = 0, rc = STLS_OK;
   bool last_df = false;
+  int pad_n0 = 0, pad_np0 = 0;
+  float *rpad = stls::tc_fd_padded_input(c->tc, &pad_n0, &pad_np0);
   for (; outer < kMaxOuter; ++outer) {
     rc = read_state();
     if (rc) return rc;
@@ -604,8 +606,13 @@ int solve_ir_impl(stls_ctx *c, const double *F, double *u, double tol, int maxit
       phase_end(c, ph);
       ph = phase_begin(c, 2);
       STLS_LAUNCH(stls::launch_cg_alpha<float>(c->pi, c->qi, N, B, c->st_in, c->rw, c->stream), "cg_alpha");
-      STLS_LAUNCH(stls::launch_cg_xr<float>(c->di, c->ri, c->pi, c->qi, N, B, eta, c->st_in, c->rw, c->stream),
-                  "cg_xr");
+      if (rpad != nullptr)  // r also goes straight into the TF32 preconditioner's input rows
+        STLS_LAUNCH(stls::launch_cg_xr_pad(c->di, c->ri, c->pi, c->qi, N, B, eta, c->st_in, c->rw, rpad, pad_n0,
+                                           pad_np0, c->stream),
+                    "cg_xr");
+      else
+        STLS_LAUNCH(stls::launch_cg_xr<float>(c->di, c->ri, c->pi, c->qi, N, B, eta, c->st_in, c->rw, c->stream),
+                    "cg_xr");
       phase_end(c, ph);
       STLS_CK(cudaMemcpyAsync(inner_host.data(), c->st_in, sizeof(CGState) * B, cudaMemcpyDeviceToHost,
                               c->stream),
@@ -617,8 +624,13 @@ int solve_ir_impl(stls_ctx *c, const double *F, double *u, double tol, int maxit
       for (int b = 0; b < B; ++b) inner_any = inner_any || inner_host[b].active;
       if (!inner_any) break;
       ph = phase_begin(c, 1);
-      c->launches += stls::tc_fd_launch_count(c->tc);
-      STLS_CK(stls::tc_fd_apply_f32(c->tc, c->ri, c->zi, c->stream), "tensor-core FD apply");
+      if (rpad != nullptr) {
+        c->launches += stls::tc_fd_launch_count(c->tc) - 1;  // no padding pass
+        STLS_CK(stls::tc_fd_apply_f32_padded(c->tc, c->zi, c->stream), "tensor-core FD apply");
+      } else {
+        c->launches += stls::tc_fd_launch_count(c->tc);
+        STLS_CK(stls::tc_fd_apply_f32(c->tc, c->ri, c->zi, c->stream), "tensor-core FD apply");
+      }
       phase_end(c, ph);
       ph = phase_begin(c, 2);
       STLS_LAUNCH(stls::launch_cg_beta<float>(c->zi, c->ri, c->qi, N, B, 1, 0, c->st_in, c->rw, c->stream),
@@ -634,14 +646,14 @@ int solve_ir_impl(stls_ctx *c, const double *F, double *u, double tol, int maxit
     }
     total_inner += std::max(its, 1);
     // ---- FP64 correction and residual ----
-    ph = phase_begin(c, 2);
-    STLS_LAUNCH(stls::launch_ir_correct(u, c->di, N, B, c->st, c->stream), "ir_correct");
-    phase_end(c, ph);
     const double predicted = worst * std::max(inner_worst, kContractFloor);
-    if (c->have_df && predicted > kDfMargin * tol && predicted > kDfFloor && total_inner < maxit) {
-      stls::dfloat *xdf = reinterpret_cast<stls::dfloat *>(xdf_buf), *ydf = reinterpret_cast<stls::dfloat *>(q64);
-      ph = phase_begin(c, 0);
-      STLS_LAUNCH(stls::launch_df_split(u, xdf, N, B, c->st, c->stream), "df_split");
+    const bool use_df = c->have_df && predicted > kDfMargin * tol && predicted > kDfFloor && total_inner < maxit;
+    stls::dfloat *xdf = reinterpret_cast<stls::dfloat *>(xdf_buf), *ydf = reinterpret_cast<stls::dfloat *>(q64);
+    ph = phase_begin(c, 2);
+    STLS_LAUNCH(stls::launch_ir_correct(u, c->di, use_df ? xdf : nullptr, N, B, c->st, c->stream), "ir_correct");
+    phase_end(c, ph);
+    if (use_df) {  // the correction kernel wrote the double-float image of u
+      ph = phase_begin(c, 4);
       rc = apply_A_df_impl(c, xdf, ydf);
       if (rc) return rc;
       phase_end(c, ph);
@@ -970,7 +982,7 @@ long long stls_launch_count(const stls_ctx *c) { return c == nullptr ? 0 : c->la
 int stls_enable_timing(stls_ctx *c, int on) {
   if (c == nullptr) return STLS_EINVAL;
   c->timing = on != 0;
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < 5; ++i) {
     c->phase_ms[i] = 0.0;
     c->phase_count[i] = 0;
   }
@@ -979,10 +991,14 @@ int stls_enable_timing(stls_ctx *c, int on) {
 }
 
 int stls_phase_times(stls_ctx *c, double *ms_out4, long long *count_out4) {
-  if (c == nullptr) return STLS_EINVAL;
-  for (int i = 0; i < 4; ++i) {
-    if (ms_out4) ms_out4[i] = c->phase_ms[i];
-    if (count_out4) count_out4[i] = c->phase_count[i];
+  return stls_phase_times_n(c, 4, ms_out4, count_out4);
+}
+
+int stls_phase_times_n(stls_ctx *c, int n, double *ms_out, long long *count_out) {
+  if (c == nullptr || n < 0) return STLS_EINVAL;
+  for (int i = 0; i < n && i < 5; ++i) {
+    if (ms_out) ms_out[i] = c->phase_ms[i];
+    if (count_out) count_out[i] = c->phase_count[i];
   }
   return STLS_OK;
 }

@@ -570,6 +570,15 @@ int tc_fd_error(const TcFd &tc) {
 
 int tc_fd_launch_count(const TcFd &tc) { return tc.launches_per_apply; }
 
+float *tc_fd_padded_input(TcFd &tc, int *n0, int *np0) {
+  return tc.rot != nullptr ? tc_fd_rot_padded_input(tc.rot, n0, np0) : nullptr;
+}
+
+cudaError_t tc_fd_apply_f32_padded(TcFd &tc, float *z, cudaStream_t s) {
+  if (tc.rot == nullptr) return cudaErrorInvalidValue;
+  return tc_fd_rot_apply_padded(tc.rot, z, s);
+}
+
 void tc_fd_destroy(TcFd &tc) {
   if (tc.fused != nullptr) tc_fd_fused_destroy(tc.fused);
   tc.fused = nullptr;

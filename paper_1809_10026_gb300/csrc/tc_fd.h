@@ -37,6 +37,10 @@ cudaError_t tc_fd_apply(TcFd &tc, const double *r, double *z, cudaStream_t s);
 // Same with FP32 r and z (inner solves of the refinement form).
 cudaError_t tc_fd_apply_f32(TcFd &tc, const float *r, float *z, cudaStream_t s);
 int tc_fd_launch_count(const TcFd &tc);
+// TF32 rotation passes only: the padded input buffer (NULL when the context
+// has no such passes), and z = P^{-1} r for an r already written there.
+float *tc_fd_padded_input(TcFd &tc, int *n0, int *np0);
+cudaError_t tc_fd_apply_f32_padded(TcFd &tc, float *z, cudaStream_t s);
 // Non-zero once a tensor-core kernel gave up on a bounded wait (host-mapped
 // flag; read it after synchronizing the stream).
 int tc_fd_error(const TcFd &tc);
@@ -60,6 +64,11 @@ cudaError_t tc_fd_rot_create(RotFd *&out, std::vector<void *> &allocs, int d, co
 template <typename IO>
 cudaError_t tc_fd_rot_apply(RotFd *f, const IO *r, IO *z, cudaStream_t s);
 int tc_fd_rot_launches(const RotFd *f);
+// The buffer the first rotation pass reads (rows of n0 FP32 values, np0 apart,
+// rounded to TF32), for producers that write r there directly, and the passes
+// alone on it.
+float *tc_fd_rot_padded_input(RotFd *f, int *n0, int *np0);
+cudaError_t tc_fd_rot_apply_padded(RotFd *f, float *z, cudaStream_t s);
 void tc_fd_rot_destroy(RotFd *f);
 // y = FP64(BF16(FP32(x))), both roundings to nearest even, as the fused kernels round r.
 cudaError_t round_bf16_launch(const double *x, double *y, long long n, cudaStream_t s);

@@ -181,11 +181,7 @@ __global__ void __launch_bounds__(kRotThreads, 1) rot_kernel(const __grid_consta
     for (long long t = blockIdx.x + static_cast<long long>(acc) * gridDim.x; t < ntiles;
          t += static_cast<long long>(kAcc) * gridDim.x, i += kAcc) {
       const uint32_t aph = static_cast<uint32_t>((i / kAcc) & 1);
-      if (!ptx::mbar_wait(tfull0 + 8 * acc, aph)) {
-        ok = 0;
-        break;
-      }
-      ptx::fence_after_sync();
+      // this lane's fiber and output offset (and eigenvalue) while the MMA runs
       const long long f = t * kFib + q * 32 + lane;
       const bool valid = f < a.rows;
       long long ob = 0;
@@ -196,6 +192,11 @@ __global__ void __launch_bounds__(kRotThreads, 1) rot_kernel(const __grid_consta
         ob = b * a.blk_out + g * a.np_next + inx;
         if (DIVIDE) ls = a.lam_s[fl];
       }
+      if (!ptx::mbar_wait(tfull0 + 8 * acc, aph)) {
+        ok = 0;
+        break;
+      }
+      ptx::fence_after_sync();
       const uint32_t tbase = tmem + acc * kAccCols + lane_base;
       for (int c0 = 0; c0 < a.np; c0 += 64) {
         uint32_t r[64];
@@ -466,6 +467,13 @@ cudaError_t tc_fd_rot_create(RotFd *&out, std::vector<void *> &allocs, int d, co
   return cudaSuccess;
 }
 
+namespace {
+
+template <typename IO>
+cudaError_t launch_passes(RotFd *f, IO *z, cudaStream_t s);
+
+}  // namespace
+
 template <typename IO>
 cudaError_t tc_fd_rot_apply(RotFd *f, const IO *r, IO *z, cudaStream_t s) {
   if (f == nullptr || f->passes.empty()) return cudaErrorNotReady;
@@ -478,6 +486,25 @@ cudaError_t tc_fd_rot_apply(RotFd *f, const IO *r, IO *z, cudaStream_t s) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
+  return launch_passes<IO>(f, z, s);
+}
+
+float *tc_fd_rot_padded_input(RotFd *f, int *n0, int *np0) {
+  if (f == nullptr) return nullptr;
+  if (n0) *n0 = f->n[0];
+  if (np0) *np0 = ceil_to(f->n[0], 4);
+  return f->inter[1];
+}
+
+cudaError_t tc_fd_rot_apply_padded(RotFd *f, float *z, cudaStream_t s) {
+  if (f == nullptr || f->passes.empty()) return cudaErrorNotReady;
+  return launch_passes<float>(f, z, s);
+}
+
+namespace {
+
+template <typename IO>
+cudaError_t launch_passes(RotFd *f, IO *z, cudaStream_t s) {
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
@@ -503,6 +530,8 @@ cudaError_t tc_fd_rot_apply(RotFd *f, const IO *r, IO *z, cudaStream_t s) {
   }
   return cudaSuccess;
 }
+
+}  // namespace
 
 template cudaError_t tc_fd_rot_apply<float>(RotFd *, const float *, float *, cudaStream_t);
 template cudaError_t tc_fd_rot_apply<double>(RotFd *, const double *, double *, cudaStream_t);
