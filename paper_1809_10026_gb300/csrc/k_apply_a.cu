@@ -18,6 +18,7 @@
 // 15 banded products per unknown in three spatial directions, each band row
 // multiplied once.
 #include <cstring>
+#include <type_traits>
 
 #include "kernels.h"
 #include "tc_ptx.cuh"
@@ -163,55 +164,48 @@ __device__ __forceinline__ void band_row(const T *__restrict__ band, int i, int 
 }
 
 // ---- directions 1 and 2 --------------------------------------------------------------
-// Columns are the (slice, i_1) pairs in order; a CTA owns C kAThreads
-// consecutive columns (C adjacent ones per thread) and
-// walks i_2.  Each row i_2 of the CTA's columns (plus P columns of halo on each
-// side) is staged in shared memory; every thread forms the direction-1 products
-// M1 x, J1 x, K1 x of its columns from their 2P+C neighbours (neighbours in
-// another slice are masked), keeps them in windows of 2P+1 rows, and emits the
-// direction-2 outputs of the row P behind.  Interior direction-2 band rows are
-// held in registers.
-template <typename T>
-constexpr int slice_cols() {
-  return 1;  // one column per thread (two in FP32 measured 4 % slower: fewer CTAs per SM)
-}
-
+// Columns are the (slice, i_1) pairs in order; a CTA owns kAThreads consecutive
+// columns (one per thread) and walks i_2.  Each row i_2 of the CTA's columns
+// (plus P columns of halo on each side) is staged in shared memory by cp.async
+// D rows ahead; every thread forms the direction-1 products M1 x, J1 x, K1 x of
+// its column from its 2P+1 neighbours, keeps them in windows of 2P+1 rows, and
+// emits the direction-2 outputs of the row P behind.  Interior direction-2
+// band rows are held in registers.  Neighbours in another slice meet the zero
+// coefficients of the band rows outside the matrix; the FP64 product also
+// masks them, so that a non-finite entry reaches no other slice (the FP32 and
+// double-float products skip the selects: their inputs are finite).
 template <typename T, int P>
-__global__ void __launch_bounds__(kAThreads) slice_kernel(const __grid_constant__ SliceArgs<T> a) {
-  constexpr int W = 2 * P + 1, D = prefetch_rows<T>(), R = D + 1, C = slice_cols<T>(), CC = C * kAThreads;
-  constexpr int RW = (CC + 2 * P + 3) / 4 * 4;
+__device__ __forceinline__ void slice_body(const SliceArgs<T> &a) {
+  constexpr int W = 2 * P + 1, D = prefetch_rows<T>(), R = D + 1;
+  constexpr int RW = (kAThreads + 2 * P + 3) / 4 * 4;
+  constexpr bool MASK = std::is_same<T, double>::value;
   __shared__ __align__(16) T ring[R][RW];
   const int tid = threadIdx.x, n1 = a.n1, n2 = a.n2, wp = a.row_stride;
   const long long area = static_cast<long long>(n1) * n2;
   const long long ncols = a.slices * n1;
-  const long long c0 = static_cast<long long>(blockIdx.x) * CC;
-  long long own[C], s[C];
-  int x[C];
-  bool act[C];
-  unsigned valid[C];  // bit w: neighbour i_1 = x - P + w lies in the slice
-  T cM[C][W], cJ[C][W], cK[C][W];
-#pragma unroll
-  for (int h = 0; h < C; ++h) {
-    const long long col = c0 + C * tid + h;
-    act[h] = col < ncols;
-    s[h] = act[h] ? col / n1 : 0;
-    x[h] = act[h] ? static_cast<int>(col - s[h] * n1) : 0;
-    own[h] = act[h] ? s[h] * area + x[h] : 0;
-    valid[h] = 0;
+  const long long col = static_cast<long long>(blockIdx.x) * kAThreads + tid;
+  const bool act = col < ncols;
+  const long long s = act ? col / n1 : 0;
+  const int x = act ? static_cast<int>(col - s * n1) : 0;
+  const long long own = act ? s * area + x : 0;
+  unsigned valid = 0;  // bit w: neighbour i_1 = x - P + w lies in the slice
+  if (MASK) {
 #pragma unroll
     for (int w = 0; w < W; ++w)
-      if (act[h] && x[h] - P + w >= 0 && x[h] - P + w < n1) valid[h] |= 1u << w;
-    load_row<T, W>(a.bM1 + static_cast<size_t>(x[h]) * wp, cM[h]);
-    load_row<T, W>(a.bJ1 + static_cast<size_t>(x[h]) * wp, cJ[h]);
-    load_row<T, W>(a.bK1 + static_cast<size_t>(x[h]) * wp, cK[h]);
+      if (act && x - P + w >= 0 && x - P + w < n1) valid |= 1u << w;
   }
+  T cM[W], cJ[W], cK[W];
+  load_row<T, W>(a.bM1 + static_cast<size_t>(x) * wp, cM);
+  load_row<T, W>(a.bJ1 + static_cast<size_t>(x) * wp, cJ);
+  load_row<T, W>(a.bK1 + static_cast<size_t>(x) * wp, cK);
   // halo columns: P on each side, loaded by threads 0 .. 2P-1
   long long halo = 0;
   bool has_halo = false;
   int hslot = 0;
   if (tid < 2 * P) {
-    const long long hc = tid < P ? c0 - P + tid : c0 + CC + (tid - P);
-    hslot = tid < P ? tid : CC + tid;
+    const long long c0 = static_cast<long long>(blockIdx.x) * kAThreads;
+    const long long hc = tid < P ? c0 - P + tid : c0 + kAThreads + (tid - P);
+    hslot = tid < P ? tid : kAThreads + tid;
     if (hc >= 0 && hc < ncols) {
       const long long hs = hc / n1;
       halo = hs * area + (hc - hs * n1);
@@ -230,80 +224,64 @@ __global__ void __launch_bounds__(kAThreads) slice_kernel(const __grid_constant_
 #pragma unroll
     for (int w = 0; w < W; ++w) iM2[w] = iJ2[w] = i2K2[w] = iK2[w] = T(0);
   }
-  const T *__restrict__ X = a.x;
-  auto issue = [&](int y) {
+  // this column's input and outputs, advanced one row (n1 values) per step
+  const T *xin = a.x + own;
+  const T *hin = a.x + halo;
+  auto issue = [&](int y, int slot) {
     if (y < n2) {
-      T *row = ring[y % R];
-#pragma unroll
-      for (int h = 0; h < C; ++h)
-        cp_async_elem(row + P + C * tid + h, X + own[h] + static_cast<long long>(y) * n1, act[h]);
-      if (tid < 2 * P) cp_async_elem(row + hslot, X + halo + static_cast<long long>(y) * n1, has_halo);
+      T *row = ring[slot];
+      cp_async_elem(row + P + tid, xin + static_cast<long long>(y) * n1, act);
+      if (tid < 2 * P) cp_async_elem(row + hslot, hin + static_cast<long long>(y) * n1, has_halo);
     }
     cp_async_commit();
   };
 #pragma unroll
-  for (int e = 0; e < D; ++e) issue(e);
-  T wm[C][W], wj[C][W], wk[C][W];
+  for (int e = 0; e < D; ++e) issue(e, e);
+  T wm[W], wj[W], wk[W];
 #pragma unroll
-  for (int h = 0; h < C; ++h)
-#pragma unroll
-    for (int w = 0; w < W; ++w) wm[h][w] = wj[h][w] = wk[h][w] = T(0);
-  bool ls_row[C], need_k = a.ls_last == nullptr;
-#pragma unroll
-  for (int h = 0; h < C; ++h) {
-    ls_row[h] = a.ls_last != nullptr && act[h] && (s[h] % a.n_t) == a.n_t - 1;
-    need_k = need_k || ls_row[h];
-  }
+  for (int w = 0; w < W; ++w) wm[w] = wj[w] = wk[w] = T(0);
+  const bool ls_row = a.ls_last != nullptr && act && (s % a.n_t) == a.n_t - 1;
+  const bool need_k = a.ls_last == nullptr || ls_row;
+  T *om_p = a.out_m + own, *oj_p = a.out_j + own;
+  T *ok_p = a.ls_last == nullptr ? a.out_k + own
+                                 : (ls_row ? a.ls_last + (s / a.n_t) * area + x : nullptr);
+  int slot = 0;  // ring slot of row yy; row yy + D goes to the slot before it
   // one row yy: direction 1 of row yy (from the staged row), then direction 2
   // of row y = yy - P with band rows c2M, c2J, c22K, c2K
   auto row_step = [&](int yy, const T(&c2M)[W], const T(&c2J)[W], const T(&c22K)[W], const T(&c2K)[W]) {
     cp_async_wait<D - 1>();
     __syncthreads();
-    T m0[C], j0[C], k0[C];
-#pragma unroll
-    for (int h = 0; h < C; ++h) m0[h] = j0[h] = k0[h] = T(0);
+    T m0 = T(0), j0 = T(0), k0 = T(0);
     if (yy < n2) {
-      const T *row = ring[yy % R] + C * tid;
-      T v[W + C - 1];
+      const T *row = ring[slot] + tid;
+      T u[W];
 #pragma unroll
-      for (int w = 0; w < W + C - 1; ++w) v[w] = row[w];
-#pragma unroll
-      for (int h = 0; h < C; ++h) {
-        T u[W];
-#pragma unroll
-        for (int w = 0; w < W; ++w) u[w] = ((valid[h] >> w) & 1u) ? v[w + h] : T(0);
-        m0[h] = band_dot(cM[h], u, T(0));
-        j0[h] = band_dot(cJ[h], u, T(0));
-        k0[h] = band_dot(cK[h], u, T(0));
+      for (int w = 0; w < W; ++w) {
+        u[w] = row[w];
+        if (MASK && !((valid >> w) & 1u)) u[w] = T(0);
       }
+      m0 = band_dot(cM, u, T(0));
+      j0 = band_dot(cJ, u, T(0));
+      k0 = band_dot(cK, u, T(0));
     }
-    issue(yy + D);
-#pragma unroll
-    for (int h = 0; h < C; ++h) {
-      slide(wm[h], m0[h]);
-      slide(wj[h], j0[h]);
-      slide(wk[h], k0[h]);
-    }
+    issue(yy + D, slot == 0 ? R - 1 : slot - 1);
+    slot = slot == R - 1 ? 0 : slot + 1;
+    slide(wm, m0);
+    slide(wj, j0);
+    slide(wk, k0);
     const int y = yy - P;
-    if (y >= 0) {
-#pragma unroll
-      for (int h = 0; h < C; ++h) {
-        if (!act[h]) continue;
-        const T om = band_dot(c2M, wm[h], T(0));
-        T oj = band_dot(c2M, wj[h], T(0));
-        oj = band_dot(c2J, wm[h], oj);
-        oj = band_dot(c22K, wk[h], oj);
-        const long long off = own[h] + static_cast<long long>(y) * n1;
-        a.out_m[off] = om;
-        a.out_j[off] = oj;
-        if (a.ls_last == nullptr || ls_row[h]) {
-          T ok = band_dot(c2M, wk[h], T(0));
-          ok = band_dot(c2K, wm[h], ok);
-          if (a.ls_last == nullptr)
-            a.out_k[off] = ok;
-          else
-            a.ls_last[(s[h] / a.n_t) * area + static_cast<long long>(y) * n1 + x[h]] = ok;
-        }
+    if (y >= 0 && act) {
+      const T om = band_dot(c2M, wm, T(0));
+      T oj = band_dot(c2M, wj, T(0));
+      oj = band_dot(c2J, wm, oj);
+      oj = band_dot(c22K, wk, oj);
+      const long long off = static_cast<long long>(y) * n1;
+      om_p[off] = om;
+      oj_p[off] = oj;
+      if (need_k) {
+        T ok = band_dot(c2M, wk, T(0));
+        ok = band_dot(c2K, wm, ok);
+        ok_p[off] = ok;
       }
     }
   };
@@ -313,21 +291,45 @@ __global__ void __launch_bounds__(kAThreads) slice_kernel(const __grid_constant_
 #pragma unroll
       for (int u = 0; u < W; ++u) row_step(yy0 + u, iM2, iJ2, i2K2, iK2);
     } else {
-#pragma unroll 1
-      for (int u = 0; u < W && yy0 + u < n2 + P; ++u) {
-        const int y = yy0 + u - P;
-        T c2M[W], c2J[W], c22K[W], c2K[W];
-        if (y >= 0) {
-          band_row<T, W>(a.bM2, y, wp, lo2, hi2, iM2, c2M);
-          band_row<T, W>(a.bJ2, y, wp, lo2, hi2, iJ2, c2J);
-          band_row<T, W>(a.b2K2, y, wp, lo2, hi2, i2K2, c22K);
-          if (need_k) band_row<T, W>(a.bK2, y, wp, lo2, hi2, iK2, c2K);
+      // boundary groups: the band rows are loaded
+      auto edge_step = [&](int u) {
+        if (yy0 + u < n2 + P) {
+          const int y = yy0 + u - P;
+          T c2M[W], c2J[W], c22K[W], c2K[W];
+          if (y >= 0) {
+            band_row<T, W>(a.bM2, y, wp, lo2, hi2, iM2, c2M);
+            band_row<T, W>(a.bJ2, y, wp, lo2, hi2, iJ2, c2J);
+            band_row<T, W>(a.b2K2, y, wp, lo2, hi2, i2K2, c22K);
+            if (need_k) band_row<T, W>(a.bK2, y, wp, lo2, hi2, iK2, c2K);
+          }
+          row_step(yy0 + u, c2M, c2J, c22K, c2K);
         }
-        row_step(yy0 + u, c2M, c2J, c22K, c2K);
+      };
+      if constexpr (sizeof(T) == 4) {
+        // unrolled: the window slides become register renames
+#pragma unroll
+        for (int u = 0; u < W; ++u) edge_step(u);
+      } else {
+        // the 8-byte types keep the loop: their register budget is spent
+#pragma unroll 1
+        for (int u = 0; u < W; ++u) edge_step(u);
       }
     }
   }
   cp_async_wait<0>();
+}
+
+// The FP32 kernel takes the compiler's register choice (four CTAs per SM);
+// the FP64 one is held to three CTAs per SM up to degree 3 (its natural count
+// allows two, and the FP64 pipe wants the extra warps); the double-float one
+// keeps its natural count.
+template <typename T, int P>
+__global__ void __launch_bounds__(kAThreads) slice_kernel(const __grid_constant__ SliceArgs<T> a) {
+  slice_body<T, P>(a);
+}
+template <int P>
+__global__ void __launch_bounds__(kAThreads, P <= 3 ? 3 : 1) slice_kernel_f64(const __grid_constant__ SliceArgs<double> a) {
+  slice_body<double, P>(a);
 }
 
 // ---- direction 3 ------------------------------------------------------------------------
@@ -522,10 +524,14 @@ long long blocks_for(long long cols) { return (cols + kAThreads - 1) / kAThreads
 
 template <typename T, int P>
 cudaError_t launch_slice_p(const SliceArgs<T> &a, cudaStream_t s) {
-  constexpr long long cc = slice_cols<T>() * kAThreads;
-  const long long g = (a.slices * a.n1 + cc - 1) / cc;
+  const long long g = (a.slices * a.n1 + kAThreads - 1) / kAThreads;
   if (g > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-  if (g > 0) slice_kernel<T, P><<<static_cast<unsigned>(g), kAThreads, 0, s>>>(a);
+  if (g > 0) {
+    if constexpr (std::is_same<T, double>::value)
+      slice_kernel_f64<P><<<static_cast<unsigned>(g), kAThreads, 0, s>>>(a);
+    else
+      slice_kernel<T, P><<<static_cast<unsigned>(g), kAThreads, 0, s>>>(a);
+  }
   return cudaGetLastError();
 }
 template <typename T, int P>
