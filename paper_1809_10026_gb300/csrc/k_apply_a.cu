@@ -20,6 +20,7 @@
 #include <cstring>
 #include <type_traits>
 
+#include "dot2f.cuh"
 #include "kernels.h"
 #include "tc_ptx.cuh"
 
@@ -419,65 +420,134 @@ __global__ void __launch_bounds__(kAThreads) zpass_kernel(const __grid_constant_
 
 // ---- time direction -------------------------------------------------------------------
 // y = K_t (x) (M_s x) + M_t (x) (J_s x), and + L_s x on the last time slice;
-// same register window and queue as the direction-3 pass.
-template <typename T, int P>
+// same register window and queue as the direction-3 pass.  Grid: x over the
+// N_s columns, y over the right-hand sides.  With FUSE (FP32) every thread
+// also accumulates (p, y) over its column, and the blocks of a right-hand side
+// combine their sums in a fixed order; the last one sets alpha.
+template <typename T, int P, bool FUSE>
 __global__ void __launch_bounds__(kAThreads) tpass_kernel(const __grid_constant__ TArgs<T> a) {
   constexpr int W = 2 * P + 1;
   const int tid = threadIdx.x;
-  const long long col = static_cast<long long>(blockIdx.x) * kAThreads + tid;
-  if (col >= a.outer * a.inner) return;  // no block-wide barrier below
-  const long long inner = a.inner, o = col / inner, cc = col - o * inner;
-  const int n = a.n, wp = a.row_stride, lo = a.lo, hi = a.hi;
-  const long long base = o * n * inner + cc;
-  const T *__restrict__ Ims = a.Ms + base;
-  const T *__restrict__ Ijs = a.Js + base;
-  auto ld = [&](const T *__restrict__ p, int r) -> T { return (r >= 0 && r < n) ? p[r * inner] : T(0); };
-  T iK[W], iM[W];
-  if (lo < hi) {
-    load_row<T, W>(a.bK + static_cast<size_t>(lo) * wp, iK);
-    load_row<T, W>(a.bM + static_cast<size_t>(lo) * wp, iM);
-  } else {
-#pragma unroll
-    for (int w = 0; w < W; ++w) iK[w] = iM[w] = T(0);
-  }
-  T wm[W], wj[W], qm[W], qj[W];
-#pragma unroll
-  for (int w = 0; w < W; ++w) {
-    wm[w] = ld(Ims, w - P);
-    wj[w] = ld(Ijs, w - P);
-    qm[w] = ld(Ims, P + 1 + w);
-    qj[w] = ld(Ijs, P + 1 + w);
-  }
-  auto emit = [&](int i, const T(&cK)[W], const T(&cM)[W]) {
-    T out = band_dot(cK, wm, T(0));
-    out = band_dot(cM, wj, out);
-    if (i == n - 1) out += a.ls_last[o * inner + cc];
-    a.y[base + static_cast<long long>(i) * inner] = out;
-  };
-  auto advance = [&](int i, int u) {
-    slide(wm, qm[u]);
-    slide(wj, qj[u]);
-    qm[u] = ld(Ims, i + P + 1 + W);
-    qj[u] = ld(Ijs, i + P + 1 + W);
-  };
-  for (int i0 = 0; i0 < n; i0 += W) {
-    if (i0 >= lo && i0 + W <= hi) {
-#pragma unroll
-      for (int u = 0; u < W; ++u) {
-        emit(i0 + u, iK, iM);
-        advance(i0 + u, u);
-      }
+  const long long inner = a.inner, o = blockIdx.y;
+  const long long cc = static_cast<long long>(blockIdx.x) * kAThreads + tid;
+  Dot2f acc;
+  if (cc < inner) {
+    const int n = a.n, wp = a.row_stride, lo = a.lo, hi = a.hi;
+    const long long base = o * n * inner + cc;
+    const T *__restrict__ Ims = a.Ms + base;
+    const T *__restrict__ Ijs = a.Js + base;
+    auto ld = [&](const T *__restrict__ p, int r) -> T { return (r >= 0 && r < n) ? p[r * inner] : T(0); };
+    T iK[W], iM[W];
+    if (lo < hi) {
+      load_row<T, W>(a.bK + static_cast<size_t>(lo) * wp, iK);
+      load_row<T, W>(a.bM + static_cast<size_t>(lo) * wp, iM);
     } else {
 #pragma unroll
-      for (int u = 0; u < W; ++u) {
-        const int i = i0 + u;
-        if (i < n) {
-          T cK[W], cM[W];
-          band_row<T, W>(a.bK, i, wp, lo, hi, iK, cK);
-          band_row<T, W>(a.bM, i, wp, lo, hi, iM, cM);
-          emit(i, cK, cM);
+      for (int w = 0; w < W; ++w) iK[w] = iM[w] = T(0);
+    }
+    T wm[W], wj[W], qm[W], qj[W];
+    float qp[W];  // FUSE: p of rows i0 + u, loaded W rows ahead
+    const float *Ip = nullptr;
+    if constexpr (FUSE) Ip = a.fuse.p + base;
+    auto ldp = [&](int r) -> float {
+      if constexpr (FUSE)
+        return r < n ? Ip[r * inner] : 0.f;
+      else
+        return 0.f;
+    };
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      wm[w] = ld(Ims, w - P);
+      wj[w] = ld(Ijs, w - P);
+      qm[w] = ld(Ims, P + 1 + w);
+      qj[w] = ld(Ijs, P + 1 + w);
+      qp[w] = ldp(w);
+    }
+    auto emit = [&](int i, int u, const T(&cK)[W], const T(&cM)[W]) {
+      T out = band_dot(cK, wm, T(0));
+      out = band_dot(cM, wj, out);
+      if (i == n - 1) out += a.ls_last[o * inner + cc];
+      a.y[base + static_cast<long long>(i) * inner] = out;
+      if constexpr (FUSE) acc.add(qp[u], out);
+    };
+    auto advance = [&](int i, int u) {
+      slide(wm, qm[u]);
+      slide(wj, qj[u]);
+      qm[u] = ld(Ims, i + P + 1 + W);
+      qj[u] = ld(Ijs, i + P + 1 + W);
+      if constexpr (FUSE) qp[u] = ldp(i + W);
+    };
+    for (int i0 = 0; i0 < n; i0 += W) {
+      if (i0 >= lo && i0 + W <= hi) {
+#pragma unroll
+        for (int u = 0; u < W; ++u) {
+          emit(i0 + u, u, iK, iM);
+          advance(i0 + u, u);
         }
-        advance(i, u);
+      } else {
+#pragma unroll
+        for (int u = 0; u < W; ++u) {
+          const int i = i0 + u;
+          if (i < n) {
+            T cK[W], cM[W];
+            band_row<T, W>(a.bK, i, wp, lo, hi, iK, cK);
+            band_row<T, W>(a.bM, i, wp, lo, hi, iM, cM);
+            emit(i, u, cK, cM);
+          }
+          advance(i, u);
+        }
+      }
+    }
+  }  // cc < inner
+  if constexpr (FUSE) {
+    // block sum in a fixed order, then the blocks of this right-hand side
+    __shared__ double sh[kAThreads / 32];
+    __shared__ bool is_last;
+    const int lane = tid & 31, wid = tid >> 5;
+    double v = acc.value();
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) v += __shfl_xor_sync(0xffffffffu, v, s);
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    const unsigned gx = gridDim.x;
+    const AlphaFuse &fz = a.fuse;
+    if (tid == 0) {
+      double t = 0.0;
+#pragma unroll
+      for (int w = 0; w < kAThreads / 32; ++w) t += sh[w];
+      fz.partials[o * gx + blockIdx.x] = t;
+      __threadfence();
+      is_last = atomicAdd(fz.tickets + o, 1u) == gx - 1;
+    }
+    __syncthreads();
+    if (is_last) {
+      __threadfence();
+      const volatile double *src = fz.partials + o * gx;
+      double t = 0.0;
+      for (unsigned g = tid; g < gx; g += kAThreads) t += src[g];
+#pragma unroll
+      for (int s = 16; s > 0; s >>= 1) t += __shfl_xor_sync(0xffffffffu, t, s);
+      __syncthreads();
+      if (lane == 0) sh[wid] = t;
+      __syncthreads();
+      if (tid == 0) {
+        double tot = 0.0;
+#pragma unroll
+        for (int w = 0; w < kAThreads / 32; ++w) tot += sh[w];
+        fz.tickets[o] = 0u;
+        CGState &st = fz.st[o];
+        if (st.active) {
+          st.pq = tot;
+          if (!isfinite(tot)) {
+            st.status = STLS_ENONFINITE;
+            st.active = 0;
+          } else if (!(tot > 0.0)) {
+            st.status = STLS_EBREAKDOWN;
+            st.active = 0;
+          } else {
+            st.alpha = st.rz / tot;
+          }
+        }
       }
     }
   }
@@ -543,9 +613,18 @@ cudaError_t launch_zpass_p(const ZArgs<T> &a, cudaStream_t s) {
 }
 template <typename T, int P>
 cudaError_t launch_tpass_p(const TArgs<T> &a, cudaStream_t s) {
-  const long long g = blocks_for(a.outer * a.inner);
-  if (g > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-  if (g > 0) tpass_kernel<T, P><<<static_cast<unsigned>(g), kAThreads, 0, s>>>(a);
+  const long long g = blocks_for(a.inner);
+  if (g > 0x7fffffffLL || a.outer > 65535) return cudaErrorInvalidConfiguration;
+  if (g > 0 && a.outer > 0) {
+    const dim3 grid(static_cast<unsigned>(g), static_cast<unsigned>(a.outer));
+    if constexpr (std::is_same<T, float>::value) {
+      if (a.fuse.p != nullptr) {
+        tpass_kernel<T, P, true><<<grid, kAThreads, 0, s>>>(a);
+        return cudaGetLastError();
+      }
+    }
+    tpass_kernel<T, P, false><<<grid, kAThreads, 0, s>>>(a);
+  }
   return cudaGetLastError();
 }
 
@@ -584,6 +663,8 @@ cudaError_t dispatch_tpass(int p, const TArgs<T> &a, cudaStream_t s) {
 }
 
 }  // namespace
+
+int alpha_blocks(long long Ns) { return static_cast<int>(blocks_for(Ns)); }
 
 int band_row_stride(int p, int elem_bytes) {
   const int w = 2 * p + 1, l = 16 / elem_bytes;
@@ -670,6 +751,7 @@ cudaError_t launch_fused_A(const FusedA<T> &f, const T *x, T *y, cudaStream_t s)
   ta.row_stride = wt;
   ta.lo = f.lo_t;
   ta.hi = f.hi_t;
+  ta.fuse = f.fuse;
   return dispatch_tpass<T>(f.p_t, ta, s);
 }
 

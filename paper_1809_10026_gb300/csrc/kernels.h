@@ -56,10 +56,22 @@ struct ZArgs {
   int n, n_t, row_stride;
   int lo, hi;              // rows [lo, hi) of the bands are all equal
 };
+// The CG step length fused into the last kernel of an FP32 A x: (p, y) per
+// right-hand side with the same compensated accumulation and deterministic
+// order as launch_cg_alpha, then alpha = rz / (p, y) with its checks.
+struct AlphaFuse {
+  const float *p;      // NULL: not fused
+  CGState *st;
+  double *partials;    // B * alpha_blocks(N_s) entries
+  unsigned *tickets;   // B entries, zero between launches
+};
+int alpha_blocks(long long Ns);
+
 template <typename T>
 struct TArgs {
   const T *Ms, *Js, *ls_last;
   T *y;
+  AlphaFuse fuse;  // FP32 only
   const T *bK, *bM;
   long long outer, inner;  // outer = B, inner = N_s
   int n, row_stride;
@@ -72,6 +84,7 @@ struct FusedA {
   const T *bKt, *bMt;                       // padded time bands
   T *work[5];                               // d = 3: m, j', k, M_s x, J_s x; d = 2: work[3..4]
   T *ls_last;                               // B * N_s
+  AlphaFuse fuse;                           // FP32: (p, A p) and alpha in the time kernel
   // rows [lo, hi) of every band of a direction are identical (the interior
   // rows of uniform-knot Galerkin matrices); lo = hi = 0 when none are
   int lo[3], hi[3], lo_t, hi_t;

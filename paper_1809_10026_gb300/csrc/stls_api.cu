@@ -57,6 +57,8 @@ struct stls_ctx {
   double *lift_tmp[4] = {};
   float *ri = nullptr, *pi = nullptr, *qi = nullptr, *zi = nullptr, *di = nullptr;  // refinement inner vectors
   CGState *st_in = nullptr;
+  double *alpha_partials = nullptr;  // fused (p, A p) of the inner solves: B * alpha_blocks(N_s)
+  unsigned *alpha_tickets = nullptr;
   double *dF = nullptr, *du = nullptr;
   CGState *st = nullptr, *st_host = nullptr;
   stls::RedWork rw{};
@@ -352,6 +354,26 @@ int apply_A_df_impl(stls_ctx *c, const stls::dfloat *x, stls::dfloat *y) {
 }
 
 template <typename T>
+int apply_A_impl(stls_ctx *c, AOps<T> &A, const T *x, T *y);
+
+// q = A p in FP32 with the inner CG's step length fused into the last kernel
+// ((p, q) and alpha = rz / (p, q) on st_in); falls back to the separate
+// product when the fused A x does not apply.
+int apply_A_f32_alpha(stls_ctx *c, const float *p, float *q) {
+  if (stls::fused_A_supported(c->d, c->hs.prm.p_s, c->hs.prm.p_t)) {
+    stls::FusedA<float> f = fused_args(c, c->a32);
+    f.fuse = {p, c->st_in, c->alpha_partials, c->alpha_tickets};
+    c->launches += c->d - 1;
+    STLS_LAUNCH(stls::launch_fused_A<float>(f, p, q, c->stream), "fused A x (with alpha)");
+    return STLS_OK;
+  }
+  int rc = apply_A_impl<float>(c, c->a32, p, q);
+  if (rc) return rc;
+  STLS_LAUNCH(stls::launch_cg_alpha<float>(p, q, c->N, c->B, c->st_in, c->rw, c->stream), "cg_alpha");
+  return STLS_OK;
+}
+
+template <typename T>
 int apply_A_impl(stls_ctx *c, AOps<T> &A, const T *x, T *y) {
   if (stls::fused_A_supported(c->d, c->hs.prm.p_s, c->hs.prm.p_t)) {
     const stls::FusedA<T> f = fused_args(c, A);
@@ -601,11 +623,10 @@ int solve_ir_impl(stls_ctx *c, const double *F, double *u, double tol, int maxit
     const int budget = std::min(maxit - total_inner, kMaxInnerPerOuter);
     for (int it = 1; it <= budget; ++it) {
       ph = phase_begin(c, 3);
-      rc = apply_A_impl<float>(c, c->a32, c->pi, c->qi);
+      rc = apply_A_f32_alpha(c, c->pi, c->qi);  // q = A p and alpha
       if (rc) return rc;
       phase_end(c, ph);
       ph = phase_begin(c, 2);
-      STLS_LAUNCH(stls::launch_cg_alpha<float>(c->pi, c->qi, N, B, c->st_in, c->rw, c->stream), "cg_alpha");
       if (rpad != nullptr)  // r also goes straight into the TF32 preconditioner's input rows
         STLS_LAUNCH(stls::launch_cg_xr_pad(c->di, c->ri, c->pi, c->qi, N, B, eta, c->st_in, c->rw, rpad, pad_n0,
                                            pad_np0, c->stream),
@@ -822,6 +843,8 @@ int stls_create(stls_ctx **out, const stls_params *prm, void *cuda_stream) {
     for (float **v : iv)
       if (!rc) rc = dev_alloc(c, v, BN);
     if (!rc) rc = dev_alloc(c, &c->st_in, c->B);
+    if (!rc) rc = dev_alloc(c, &c->alpha_partials, static_cast<size_t>(c->B) * stls::alpha_blocks(c->Ns));
+    if (!rc) rc = dev_alloc(c, &c->alpha_tickets, c->B);
   }
   for (int a = 0; a < 4 && !rc; ++a) rc = dev_alloc(c, &c->lift_tmp[a], BNs);
   if (!rc) rc = dev_alloc(c, &c->st, c->B);
@@ -836,7 +859,8 @@ int stls_create(stls_ctx **out, const stls_params *prm, void *cuda_stream) {
   }
   if (cudaMemset(c->rw.tickets, 0, sizeof(unsigned) * c->B) != cudaSuccess ||
       cudaMemset(c->st, 0, sizeof(CGState) * c->B) != cudaSuccess ||
-      (c->st_in != nullptr && cudaMemset(c->st_in, 0, sizeof(CGState) * c->B) != cudaSuccess)) {
+      (c->st_in != nullptr && cudaMemset(c->st_in, 0, sizeof(CGState) * c->B) != cudaSuccess) ||
+      (c->alpha_tickets != nullptr && cudaMemset(c->alpha_tickets, 0, sizeof(unsigned) * c->B) != cudaSuccess)) {
     c->err = "cudaMemset failed";
     return fail(STLS_ECUDA);
   }
