@@ -191,6 +191,8 @@ def timed_solves(S, F, u, tol, steps, warmup, world, timing):
 TRAFFIC = {
     # fused BF16 FD apply with FP32 in/out: 5 kernels, 234.8 MB read + 19.1 MB written
     ("precond", "bf16", True): 253888256,
+    # TF32 FD apply inside the inner loop: 8 rotation passes, 650.3 MB read + 155.8 MB written
+    ("precond", "tf32", True): 806137856,
 }
 
 
