@@ -155,6 +155,30 @@ struct PadOut {
   int n, np;
 };
 
+// Offset of entry i of one right-hand side in the padded rows
+// (i + (i / n)(np - n)), for i = i0, i0 + S, i0 + 2S, ..., without divisions.
+struct PadIter {
+  unsigned off = 0, soff = 0;
+  int col = 0, scol = 0, n = 1, gap = 0;
+  __device__ __forceinline__ PadIter(long long i0, long long S, const PadOut &p) {
+    const long long row = i0 / p.n, srow = S / p.n;
+    n = p.n;
+    gap = p.np - p.n;
+    col = static_cast<int>(i0 - row * p.n);
+    scol = static_cast<int>(S - srow * p.n);
+    off = static_cast<unsigned>(row * p.np + col);
+    soff = static_cast<unsigned>(srow * p.np + scol);
+  }
+  __device__ __forceinline__ void next() {
+    off += soff;
+    col += scol;
+    if (col >= n) {
+      col -= n;
+      off += gap;
+    }
+  }
+};
+
 // (8 blocks of 256 threads per SM: the reduction grid is sized for that)
 template <typename T, bool PAD = false>
 __global__ void __launch_bounds__(kThreads, 8)
@@ -171,32 +195,16 @@ __global__ void __launch_bounds__(kThreads, 8)
       Dot2f acc;
       const long long i0 = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x;
       const long long S = static_cast<long long>(gridDim.x) * kThreads;
-      // offset of entry i in the padded copy (i + (i / n) (np - n)), advanced
-      // without divisions: col = i mod n
-      unsigned off = 0, soff = 0;
-      int col = 0, scol = 0;
-      float *pb_out = nullptr;
-      if (PAD) {
-        const long long row = i0 / pad.n, srow = S / pad.n;
-        col = static_cast<int>(i0 - row * pad.n);
-        scol = static_cast<int>(S - srow * pad.n);
-        off = static_cast<unsigned>(row * pad.np + col);
-        soff = static_cast<unsigned>(srow * pad.np + scol);
-        pb_out = pad.out + static_cast<size_t>(b) * (N / pad.n) * pad.np;
-      }
+      PadIter it(i0, S, PAD ? pad : PadOut{nullptr, 1, 1});
+      float *pb_out = PAD ? pad.out + static_cast<size_t>(b) * (N / pad.n) * pad.np : nullptr;
       for (long long i = i0; i < N; i += S) {
         xb[i] = fma(alpha, pb[i], xb[i]);
         const T ri = fma(-alpha, qb[i], rb[i]);
         rb[i] = ri;
         acc.add(ri, ri);
         if (PAD) {
-          pb_out[off] = ptx::tf32_rna(ri);
-          off += soff;
-          col += scol;
-          if (col >= pad.n) {
-            col -= pad.n;
-            off += pad.np - pad.n;
-          }
+          pb_out[it.off] = ptx::tf32_rna(ri);
+          it.next();
         }
       }
       v[0] = acc.value();
@@ -317,18 +325,26 @@ __global__ void __launch_bounds__(kThreads, 8)
 // norm is accumulated by Dot2f.
 __global__ void __launch_bounds__(kThreads, 8)
     ir_start_kernel(const double *__restrict__ r64, float *__restrict__ r32, float *__restrict__ d,
-                    long long N, const CGState *outer, CGState *inner, RedWork rw) {
+                    long long N, const CGState *outer, CGState *inner, RedWork rw, PadOut pad) {
   const int b = blockIdx.y;
   const int k = ptx::df_scale_exp(outer[b].rr);
   const double *rb = r64 + static_cast<size_t>(b) * N;
   float *ib = r32 + static_cast<size_t>(b) * N, *db = d + static_cast<size_t>(b) * N;
   Dot2f acc;
-  for (long long i = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x; i < N;
-       i += static_cast<long long>(gridDim.x) * kThreads) {
+  const long long i0 = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x;
+  const long long S = static_cast<long long>(gridDim.x) * kThreads;
+  const bool padded = pad.out != nullptr;
+  PadIter it(i0, S, padded ? pad : PadOut{nullptr, 1, 1});
+  float *pb_out = padded ? pad.out + static_cast<size_t>(b) * (N / pad.n) * pad.np : nullptr;
+  for (long long i = i0; i < N; i += S) {
     const float x = ptx::f64_to_f32_rn(ptx::scale_f64(rb[i], -k));
     ib[i] = x;
     db[i] = 0.f;
     acc.add(x, x);
+    if (padded) {
+      pb_out[it.off] = ptx::tf32_rna(x);
+      it.next();
+    }
   }
   double v[1] = {acc.value()};
   double tot[1];
@@ -539,8 +555,11 @@ cudaError_t launch_cg_xr_pad(float *x, float *r, const float *p, const float *q,
   return cudaGetLastError();
 }
 cudaError_t launch_ir_start(const double *r64, float *r32, float *d, long long N, int B, const CGState *outer,
-                            CGState *inner, RedWork rw, cudaStream_t s) {
-  ir_start_kernel<<<dim3(rw.grid, B), kThreads, 0, s>>>(r64, r32, d, N, outer, inner, rw);
+                            CGState *inner, RedWork rw, float *rpad, int n0, int np0, cudaStream_t s) {
+  if (rpad != nullptr && (n0 < 1 || np0 < n0 || N % n0 != 0 || static_cast<double>(N / n0) * np0 >= 4294967296.0))
+    return cudaErrorInvalidValue;
+  const PadOut pad{rpad, rpad != nullptr ? n0 : 1, rpad != nullptr ? np0 : 1};
+  ir_start_kernel<<<dim3(rw.grid, B), kThreads, 0, s>>>(r64, r32, d, N, outer, inner, rw, pad);
   return cudaGetLastError();
 }
 cudaError_t launch_ir_correct(double *u, const float *d, dfloat *udf, long long N, int B, const CGState *outer,

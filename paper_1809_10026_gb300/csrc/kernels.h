@@ -175,8 +175,10 @@ cudaError_t launch_cg_p(const T *z, T *p, long long N, int B, int first, CGState
 // Refinement form: FP32 inner right-hand side r64 2^-k (||r64|| = f 2^k,
 // f in [0.5, 1)), FP64 correction of u, FP64 residual F - A u with the outer
 // convergence test.
+// (rpad != NULL: also r32 rounded to TF32 into rows of n0 values np0 apart,
+// as launch_cg_xr_pad writes them.)
 cudaError_t launch_ir_start(const double *r64, float *r32, float *d, long long N, int B, const CGState *outer,
-                            CGState *inner, RedWork rw, cudaStream_t s);
+                            CGState *inner, RedWork rw, float *rpad, int n0, int np0, cudaStream_t s);
 // u += 2^k d (k: exponent of ||r64||, as ir_start scaled); with udf != NULL
 // also writes launch_df_split's image of the new u (scale from outer).
 cudaError_t launch_ir_correct(double *u, const float *d, dfloat *udf, long long N, int B, const CGState *outer,

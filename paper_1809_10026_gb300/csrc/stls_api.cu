@@ -609,11 +609,18 @@ int solve_ir_impl(stls_ctx *c, const double *F, double *u, double tol, int maxit
     }
     // ---- inner flexible CG in FP32 on A d = r / ||r|| ----
     ph = phase_begin(c, 2);
-    STLS_LAUNCH(stls::launch_ir_start(r64, c->ri, c->di, N, B, c->st, c->st_in, c->rw, c->stream), "ir_start");
+    STLS_LAUNCH(stls::launch_ir_start(r64, c->ri, c->di, N, B, c->st, c->st_in, c->rw, rpad, pad_n0, pad_np0,
+                                      c->stream),
+                "ir_start");
     phase_end(c, ph);
     ph = phase_begin(c, 1);
-    c->launches += stls::tc_fd_launch_count(c->tc);
-    STLS_CK(stls::tc_fd_apply_f32(c->tc, c->ri, c->zi, c->stream), "tensor-core FD apply");
+    if (rpad != nullptr) {  // ir_start wrote r into the preconditioner's input rows
+      c->launches += stls::tc_fd_launch_count(c->tc) - 1;
+      STLS_CK(stls::tc_fd_apply_f32_padded(c->tc, c->zi, c->stream), "tensor-core FD apply");
+    } else {
+      c->launches += stls::tc_fd_launch_count(c->tc);
+      STLS_CK(stls::tc_fd_apply_f32(c->tc, c->ri, c->zi, c->stream), "tensor-core FD apply");
+    }
     phase_end(c, ph);
     ph = phase_begin(c, 2);
     STLS_LAUNCH(stls::launch_cg_beta<float>(c->zi, c->ri, c->qi, N, B, 1, 1, c->st_in, c->rw, c->stream),
