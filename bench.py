@@ -12,12 +12,14 @@ preconditioner apply with FP32 accumulation, FP64 outer residual F - A u
 (iterative refinement around a flexible CG in FP32 with FP64-accumulated inner
 products; the outer steps before the last take a provisional residual with
 the double-float A x).  The other forms are measured on the same workload in
-the same run and reported under "forms": BF16 refinement, the strict BF16
-form (flexible CG with FP64 vectors, FP64 A x, only the preconditioner in
-BF16) and the FP64 PCG.
+the same run and reported under "forms": the same with every outer residual
+in FP64 ("_ir64"), BF16 refinement (both residual variants), the strict
+TF32 and BF16 forms (flexible CG with FP64 vectors, FP64 A x, only the
+preconditioner in TF32/BF16) and the FP64 PCG.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--precision tf32|bf16|fp64] [--no-refine] [--forms a,b,...]
+                  [--precision tf32|bf16|fp64] [--no-refine] [--fp64-residuals]
+                  [--forms a,b,...]
 
 With --gpus N > 1 (under torchrun) every rank solves its own copy of the
 workload (replicas; the method has no data-path exchange on one node) and
@@ -45,9 +47,13 @@ WORKLOAD = dict(name="cube3d_p3_n64", d=3, p=3, n_el=64, T=1.0, tol=1e-8, tag=4,
 FP64_ITERS = 17
 PAPER_DOFS = 18125250 / 227.93  # Table 1, p = 3, n_sub = 64: serial Matlab, i7-5820K (context)
 METRIC = "PCG solve DoF/s at relative residual 1e-8 (mixed BF16 form vs FP64 form)"
-# form name -> (precision, refine)
-FORMS = {"bf16_ir": ("bf16", True), "tf32_ir": ("tf32", True), "bf16_fcg": ("bf16", False),
-         "tf32_fcg": ("tf32", False), "fp64_pcg": ("fp64", False)}
+# form name -> (precision, refine, every outer residual in FP64); the "_ir"
+# forms take provisional double-float outer residuals before the last one,
+# the "_ir64" forms take every outer residual in FP64
+FORMS = {"bf16_ir": ("bf16", True, False), "tf32_ir": ("tf32", True, False),
+         "bf16_ir64": ("bf16", True, True), "tf32_ir64": ("tf32", True, True),
+         "bf16_fcg": ("bf16", False, False), "tf32_fcg": ("tf32", False, False),
+         "fp64_pcg": ("fp64", False, False)}
 
 
 def load_peaks():
@@ -243,8 +249,9 @@ def roofline_entry(phase, ms, count, S, p, peaks, refine):
 
 def run_form(stls, name, W, F, args, world, sampler=None):
     import torch
-    precision, refine = FORMS[name]
+    precision, refine, fp64_res = FORMS[name]
     S = stls.Solver(W["d"], W["p"], W["n_el"], W["T"], precision=precision, refine=refine,
+                    fp64_residuals=fp64_res,
                     device=F.device)
     u = torch.empty_like(F)
     steps = args.steps if sampler is not None else max(1, min(args.steps, args.form_steps))
@@ -297,7 +304,8 @@ def run_ours(args):
     device = torch.device("cuda", local)
     peaks = load_peaks()
     W = WORKLOAD
-    head = args.precision + ("_ir" if (args.precision != "fp64" and not args.no_refine) else
+    head = args.precision + ("_ir" + ("64" if args.fp64_residuals else "")
+                             if (args.precision != "fp64" and not args.no_refine) else
                              ("_fcg" if args.precision != "fp64" else "_pcg"))
     extra = [f for f in args.forms.split(",") if f and f != head] if args.forms else []
     for f in extra:
@@ -340,8 +348,9 @@ def run_ours(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": {"bf16_ir": "bf16+f32+f64", "tf32_ir": "tf32+f32+f64", "bf16_fcg": "bf16+f64",
-                  "tf32_fcg": "tf32+f64", "fp64_pcg": "f64"}[head],
+        "dtype": {"bf16_ir": "bf16+f32+f64", "tf32_ir": "tf32+f32+f64", "bf16_ir64": "bf16+f32+f64",
+                  "tf32_ir64": "tf32+f32+f64", "bf16_fcg": "bf16+f64", "tf32_fcg": "tf32+f64",
+                  "fp64_pcg": "f64"}[head],
         "data": "synthetic",
         "config": {"workload": W["name"], "description": W["text"], "form": head,
                    "parallelism": "replicas" if world > 1 else "single GPU",
@@ -457,9 +466,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp64", "tf32", "bf16"], default="tf32")
+    ap.add_argument("--fp64-residuals", action="store_true",
+                    help="headline refinement form with every outer residual in FP64")
     ap.add_argument("--no-refine", action="store_true",
                     help="headline mixed form without the FP64 outer residual (strict flexible CG)")
-    ap.add_argument("--forms", default="bf16_ir,bf16_fcg,fp64_pcg",
+    ap.add_argument("--forms", default="tf32_ir64,bf16_ir,bf16_ir64,tf32_fcg,bf16_fcg,fp64_pcg",
                     help="other forms timed in the same run (comma separated; empty for none)")
     ap.add_argument("--form-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")

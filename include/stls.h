@@ -82,6 +82,9 @@ typedef struct {
                        over K = ceil(log R / log 1e-3) outer steps, inner
                        tolerance R^(1/K) clamped to [1e-4, 0.1]; at most 400
                        inner iterations per outer step */
+  int fp64_residuals; /* refine = 1 only.  0: provisional double-float outer
+                       residuals as described under refine; 1: every outer
+                       residual F - A u in FP64 */
 } stls_params;
 
 typedef struct {

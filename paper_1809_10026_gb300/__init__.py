@@ -62,7 +62,8 @@ class Solver:
     """
 
     def __init__(self, d, p, n_el, T=1.0, precision="fp64", flexible=None, batch=1, p_t=None,
-                 n_el_t=None, time_pencil="physical", device=None, refine=False, inner_tol=0.0):
+                 n_el_t=None, time_pencil="physical", device=None, refine=False, inner_tol=0.0,
+                 fp64_residuals=False):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("stls.Solver needs a CUDA device (no CPU fallback)")
@@ -70,7 +71,7 @@ class Solver:
         self.device = torch.device("cuda" if device is None else device)
         self.lib = _lib.load()
         self.params = make_params(d, p, n_el, T, precision, flexible, batch, p_t, n_el_t, time_pencil,
-                                  refine, inner_tol)
+                                  refine, inner_tol, fp64_residuals)
         self.ctx = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             stream = torch.cuda.current_stream(self.device).cuda_stream

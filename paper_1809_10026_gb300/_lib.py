@@ -21,7 +21,8 @@ class Params(ctypes.Structure):
     _fields_ = [("d", ctypes.c_int), ("p_s", ctypes.c_int), ("p_t", ctypes.c_int),
                 ("n_el_s", ctypes.c_int * 3), ("n_el_t", ctypes.c_int), ("T", ctypes.c_double),
                 ("precision", ctypes.c_int), ("flexible", ctypes.c_int), ("batch", ctypes.c_int),
-                ("time_pencil", ctypes.c_int), ("refine", ctypes.c_int), ("inner_tol", ctypes.c_double)]
+                ("time_pencil", ctypes.c_int), ("refine", ctypes.c_int), ("inner_tol", ctypes.c_double),
+                ("fp64_residuals", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -79,7 +80,7 @@ def load():
 
 
 def make_params(d, p, n_el, T=1.0, precision="fp64", flexible=None, batch=1, p_t=None, n_el_t=None,
-                time_pencil="physical", refine=False, inner_tol=0.0):
+                time_pencil="physical", refine=False, inner_tol=0.0, fp64_residuals=False):
     n_el_s = [int(n_el)] * d if isinstance(n_el, int) else [int(v) for v in n_el]
     if len(n_el_s) != d:
         raise ValueError("n_el must be an int or a list of d ints")
@@ -97,4 +98,5 @@ def make_params(d, p, n_el, T=1.0, precision="fp64", flexible=None, batch=1, p_t
     prm.time_pencil = {"physical": 0, "hat": 1}[time_pencil]
     prm.refine = int(bool(refine))
     prm.inner_tol = float(inner_tol)
+    prm.fp64_residuals = int(bool(fp64_residuals))
     return prm

@@ -37,6 +37,7 @@ std::string validate_params(const stls_params &prm) {
   if (prm.refine != 0 && prm.refine != 1) return "refine must be 0 or 1";
   if (prm.refine == 1 && prm.precision == STLS_FP64) return "refine = 1 needs a mixed precision form";
   if (!(prm.inner_tol >= 0.0) || !(prm.inner_tol < 1.0)) return "inner_tol must be in [0, 1)";
+  if (prm.fp64_residuals != 0 && prm.fp64_residuals != 1) return "fp64_residuals must be 0 or 1";
   return "";
 }
 

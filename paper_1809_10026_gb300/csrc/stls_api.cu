@@ -783,7 +783,7 @@ int stls_create(stls_ctx **out, const stls_params *prm, void *cuda_stream) {
   int rc = STLS_OK;
   const bool refine = P.refine != 0;
   // double-float A x for the provisional outer residuals of the refinement form
-  const bool df = refine && stls::fused_A_supported(c->d, P.p_s, P.p_t);
+  const bool df = refine && P.fp64_residuals == 0 && stls::fused_A_supported(c->d, P.p_s, P.p_t);
   c->have_df = df;
   auto to_f32 = [](const std::vector<double> &v) { return std::vector<float>(v.begin(), v.end()); };
   for (int k = 0; k < c->d && !rc; ++k) {

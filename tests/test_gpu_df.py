@@ -134,3 +134,23 @@ def test_cfg4_df_residual_accuracy():
           "| ||r_64|| / ||F|| =", torch.linalg.norm(r64).item() / nF, "| outer", info[0]["outer"],
           "of which double-float", info[0]["outer_df"])
     assert delta <= 1e-10, delta
+
+
+@pytest.mark.parametrize("form", ["bf16", "tf32"])
+def test_refinement_fp64_residuals_option(form):
+    """fp64_residuals = 1: every outer residual in FP64 (no provisional double-float
+    ones); the solve reaches the same tolerance and agrees with the default."""
+    pi = np.pi
+    prob = STProblem(3, 4, 32)
+    s = lambda x: np.sin(pi * x)
+    F = _cuda(prob.load_separable([(1.0, np.cos, [s, s, s]), (3 * pi ** 2, np.sin, [s, s, s])]))
+    S64 = _solver(3, 4, 32, precision=form, refine=True, fp64_residuals=True)
+    u64, i64 = S64.solve(F, tol=1e-12, maxit=800)
+    assert i64[0]["status"] == "ok" and i64[0]["true_rel_res"] <= 1e-12 and i64[0]["outer_df"] == 0
+    Sdf = _solver(3, 4, 32, precision=form, refine=True)
+    udf, idf = Sdf.solve(F, tol=1e-12, maxit=800)
+    assert idf[0]["status"] == "ok" and idf[0]["true_rel_res"] <= 1e-12 and idf[0]["outer_df"] >= 1
+    rel = (torch.linalg.norm(udf - u64) / torch.linalg.norm(u64)).item()
+    assert rel <= 1e-8, rel
+    with pytest.raises(RuntimeError, match="apply_A_df"):
+        S64.apply_A_df(F)

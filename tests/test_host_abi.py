@@ -33,7 +33,7 @@ def test_exports_every_declared_symbol(lib):
 
 
 @pytest.mark.parametrize("bad", [dict(d=4), dict(p_s=1), dict(T=0.0), dict(T=float("nan")),
-                                 dict(n_el_t=0), dict(batch=0), dict(precision=7)])
+                                 dict(n_el_t=0), dict(batch=0), dict(precision=7), dict(fp64_residuals=2)])
 def test_invalid_parameters_rejected_on_host(lib, bad):
     prm = _lib.make_params(2, 3, 4)
     for k, v in bad.items():
