@@ -447,7 +447,7 @@ def run_reference(args):
         "ms_per_step": t_iter * 1e3,
         "higher_is_better": True,
         "scaling": "weak",
-        "vs_baseline": value / PAPER_DOFS,
+        "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": W["name"], "description": W["text"], "form": "fp64 oracle PCG (CPU)"},
