@@ -199,6 +199,10 @@ TRAFFIC = {
     ("precond", "bf16", True): 253888256,
     # TF32 FD apply inside the inner loop: 8 rotation passes, 650.3 MB read + 155.8 MB written
     ("precond", "tf32", True): 806137856,
+    # FP32 A x of the inner loop (slice, direction 3, time with (p, A p)): 509.1 MB read + 307.8 MB
+    # written; the same kernels serve both refinement forms
+    ("apply_A_f32", "tf32", True): 816874240,
+    ("apply_A_f32", "bf16", True): 816874240,
 }
 
 
