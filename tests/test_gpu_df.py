@@ -154,3 +154,24 @@ def test_refinement_fp64_residuals_option(form):
     assert rel <= 1e-8, rel
     with pytest.raises(RuntimeError, match="apply_A_df"):
         S64.apply_A_df(F)
+
+
+def test_phase_times_count_the_outer_steps():
+    """Phase timing of a refinement solve: one FP64 A x per FP64 outer residual,
+    one double-float A x per provisional one, one FP32 A x (with the fused
+    step length) and one preconditioner apply per inner iteration."""
+    S = _solver(3, 3, 8, precision="tf32", refine=True)
+    F = _cuda(synth.uniform(S.N, 11))
+    S.solve(F, tol=1e-8, maxit=200)  # warm-up
+    S.enable_timing(True)
+    u, info = S.solve(F, tol=1e-8, maxit=200)
+    ph = S.phase_times()
+    S.enable_timing(False)
+    it = info[0]
+    assert it["status"] == "ok" and it["outer_df"] >= 1
+    assert set(ph) == {"apply_A", "precond", "cg_vectors", "apply_A_f32", "apply_A_df"}
+    assert ph["apply_A_df"][1] == it["outer_df"]
+    assert ph["apply_A"][1] == it["outer"] - it["outer_df"]
+    assert ph["apply_A_f32"][1] == it["iters"]
+    assert ph["precond"][1] == it["iters"]  # one apply per outer step's start, one per further iteration
+    assert all(v[0] >= 0.0 for v in ph.values())
