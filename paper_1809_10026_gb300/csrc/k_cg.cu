@@ -180,7 +180,9 @@ struct PadIter {
 };
 
 // (8 blocks of 256 threads per SM: the reduction grid is sized for that)
-template <typename T, bool PAD = false>
+// DEFER: x += alpha p is left to the next p update (launch_cg_p with x), or to
+// launch_cg_x_pending once the loop ends; xpend records that it is owed.
+template <typename T, bool PAD = false, bool DEFER = false>
 __global__ void __launch_bounds__(kThreads, 8)
     cg_xr_kernel(T *__restrict__ x, T *__restrict__ r, const T *__restrict__ p,
                  const T *__restrict__ q, long long N, double tol, CGState *st, RedWork rw, PadOut pad = {}) {
@@ -198,7 +200,7 @@ __global__ void __launch_bounds__(kThreads, 8)
       PadIter it(i0, S, PAD ? pad : PadOut{nullptr, 1, 1});
       float *pb_out = PAD ? pad.out + static_cast<size_t>(b) * (N / pad.n) * pad.np : nullptr;
       for (long long i = i0; i < N; i += S) {
-        xb[i] = fma(alpha, pb[i], xb[i]);
+        if (!DEFER) xb[i] = fma(alpha, pb[i], xb[i]);
         const T ri = fma(-alpha, qb[i], rb[i]);
         rb[i] = ri;
         acc.add(ri, ri);
@@ -223,6 +225,7 @@ __global__ void __launch_bounds__(kThreads, 8)
     CGState &s = st[b];
     if (!s.active) return;
     s.iters += 1;
+    if (DEFER) s.xpend = 1;
     s.rr = tot[0];
     s.rel_res = sqrt(tot[0] / s.nF2);
     if (!isfinite(tot[0])) {
@@ -292,15 +295,54 @@ __global__ void __launch_bounds__(kThreads, 8)
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 8)
     cg_p_kernel(const T *__restrict__ z, T *__restrict__ p, long long N, int first,
-                const CGState *st) {
+                CGState *st, T *__restrict__ x, unsigned *tickets) {
   const int b = blockIdx.y;
   if (!st[b].active) return;
   const T beta = static_cast<T>(st[b].beta);
   const T *zb = z + static_cast<size_t>(b) * N;
   T *pb = p + static_cast<size_t>(b) * N;
+  if (x != nullptr && !first) {
+    // the x update deferred by cg_xr: x += alpha p with the p it used
+    const T alpha = static_cast<T>(st[b].alpha);
+    T *xb = x + static_cast<size_t>(b) * N;
+    for (long long i = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x; i < N;
+         i += static_cast<long long>(gridDim.x) * kThreads) {
+      const T po = pb[i];
+      xb[i] = fma(alpha, po, xb[i]);
+      pb[i] = fma(beta, po, zb[i]);
+    }
+    // the last block clears the flag (every block has read the state by then)
+    __shared__ bool is_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      is_last = atomicAdd(tickets + b, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (is_last && threadIdx.x == 0) {
+      st[b].xpend = 0;
+      tickets[b] = 0u;
+    }
+    return;
+  }
   for (long long i = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x; i < N;
        i += static_cast<long long>(gridDim.x) * kThreads)
     pb[i] = first ? zb[i] : fma(beta, pb[i], zb[i]);
+}
+
+// x += alpha p for the right-hand sides whose deferred update is still owed
+// (xpend) when the CG loop ends.
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 8)
+    cg_x_pending_kernel(T *__restrict__ x, const T *__restrict__ p, long long N, const CGState *st) {
+  const int b = blockIdx.y;
+  if (!st[b].xpend) return;
+  const T alpha = static_cast<T>(st[b].alpha);
+  T *xb = x + static_cast<size_t>(b) * N;
+  const T *pb = p + static_cast<size_t>(b) * N;
+  for (long long i = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x; i < N;
+       i += static_cast<long long>(gridDim.x) * kThreads)
+    xb[i] = fma(alpha, pb[i], xb[i]);
 }
 
 __global__ void __launch_bounds__(kThreads, 8)
@@ -353,6 +395,7 @@ __global__ void __launch_bounds__(kThreads, 8)
     s.nF2 = tot[0];
     s.rr = tot[0];
     s.iters = 0;
+    s.xpend = 0;
     s.status = 0;
     s.rel_res = 1.0;
     s.alpha = s.beta = s.pq = s.rz = 0.0;
@@ -531,8 +574,14 @@ cudaError_t launch_cg_beta(const T *z, const T *r, const T *q, long long N, int 
   return cudaGetLastError();
 }
 template <typename T>
-cudaError_t launch_cg_p(const T *z, T *p, long long N, int B, int first, CGState *st, cudaStream_t s) {
-  cg_p_kernel<T><<<dim3(grid_1d(N), B), kThreads, 0, s>>>(z, p, N, first, st);
+cudaError_t launch_cg_p(const T *z, T *p, long long N, int B, int first, CGState *st, cudaStream_t s, T *x,
+                        unsigned *tickets) {
+  if (x != nullptr && tickets == nullptr) return cudaErrorInvalidValue;
+  cg_p_kernel<T><<<dim3(grid_1d(N), B), kThreads, 0, s>>>(z, p, N, first, st, x, tickets);
+  return cudaGetLastError();
+}
+cudaError_t launch_cg_x_pending(float *x, const float *p, long long N, int B, const CGState *st, cudaStream_t s) {
+  cg_x_pending_kernel<float><<<dim3(grid_1d(N), B), kThreads, 0, s>>>(x, p, N, st);
   return cudaGetLastError();
 }
 #define STLS_INST(T)                                                                                       \
@@ -542,16 +591,20 @@ cudaError_t launch_cg_p(const T *z, T *p, long long N, int B, int first, CGState
                                        RedWork, cudaStream_t);                                             \
   template cudaError_t launch_cg_beta<T>(const T *, const T *, const T *, long long, int, int, int,        \
                                          CGState *, RedWork, cudaStream_t);                                \
-  template cudaError_t launch_cg_p<T>(const T *, T *, long long, int, int, CGState *, cudaStream_t);
+  template cudaError_t launch_cg_p<T>(const T *, T *, long long, int, int, CGState *, cudaStream_t, T *,  \
+                                      unsigned *);
 STLS_INST(double)
 STLS_INST(float)
 #undef STLS_INST
 cudaError_t launch_cg_xr_pad(float *x, float *r, const float *p, const float *q, long long N, int B, double tol,
-                             CGState *st, RedWork rw, float *rpad, int n0, int np0, cudaStream_t s) {
+                             CGState *st, RedWork rw, float *rpad, int n0, int np0, int defer, cudaStream_t s) {
   if (n0 < 1 || np0 < n0 || N % n0 != 0 || static_cast<double>(N / n0) * np0 >= 4294967296.0)
     return cudaErrorInvalidValue;
   PadOut pad{rpad, n0, np0};
-  cg_xr_kernel<float, true><<<dim3(rw.grid, B), kThreads, 0, s>>>(x, r, p, q, N, tol, st, rw, pad);
+  if (defer)
+    cg_xr_kernel<float, true, true><<<dim3(rw.grid, B), kThreads, 0, s>>>(x, r, p, q, N, tol, st, rw, pad);
+  else
+    cg_xr_kernel<float, true><<<dim3(rw.grid, B), kThreads, 0, s>>>(x, r, p, q, N, tol, st, rw, pad);
   return cudaGetLastError();
 }
 cudaError_t launch_ir_start(const double *r64, float *r32, float *d, long long N, int B, const CGState *outer,

@@ -145,6 +145,7 @@ inline cudaError_t launch_banded_f64(const BandSpec &spec, const ModeView &v, cu
 struct CGState {
   double rz, pq, alpha, beta, rr, nF2, rel_res, true_rr;
   int active, iters, status, df_iters;  // df_iters: provisional double-float residuals
+  int xpend;  // deferred x update: alpha p of the last x, r update is still owed to x
 };
 struct RedWork {
   double *partials;    // [batch][grid][2]
@@ -165,13 +166,20 @@ cudaError_t launch_cg_xr(T *x, T *r, const T *p, const T *q, long long N, int B,
                          RedWork rw, cudaStream_t s);
 // cg_xr in FP32 that also writes r rounded to TF32 into rows of n0 values
 // np0 apart (per right-hand side: N / n0 rows), the TF32 preconditioner's input.
+// defer != 0: x is not updated here (see launch_cg_p).
 cudaError_t launch_cg_xr_pad(float *x, float *r, const float *p, const float *q, long long N, int B, double tol,
-                             CGState *st, RedWork rw, float *rpad, int n0, int np0, cudaStream_t s);
+                             CGState *st, RedWork rw, float *rpad, int n0, int np0, int defer, cudaStream_t s);
 template <typename T>
 cudaError_t launch_cg_beta(const T *z, const T *r, const T *q, long long N, int B, int flexible, int first,
                            CGState *st, RedWork rw, cudaStream_t s);
+// With x != NULL (FP32 inner solves after launch_cg_xr_pad with defer): also
+// the deferred x += alpha p with the old p; `tickets` (zero between kernels)
+// lets the last block clear the owed-update flag.
 template <typename T>
-cudaError_t launch_cg_p(const T *z, T *p, long long N, int B, int first, CGState *st, cudaStream_t s);
+cudaError_t launch_cg_p(const T *z, T *p, long long N, int B, int first, CGState *st, cudaStream_t s,
+                        T *x = nullptr, unsigned *tickets = nullptr);
+// x += alpha p where an x update deferred by launch_cg_xr_pad is still owed.
+cudaError_t launch_cg_x_pending(float *x, const float *p, long long N, int B, const CGState *st, cudaStream_t s);
 // Refinement form: FP32 inner right-hand side r64 2^-k (||r64|| = f 2^k,
 // f in [0.5, 1)), FP64 correction of u, FP64 residual F - A u with the outer
 // convergence test.

@@ -634,9 +634,9 @@ int solve_ir_impl(stls_ctx *c, const double *F, double *u, double tol, int maxit
       if (rc) return rc;
       phase_end(c, ph);
       ph = phase_begin(c, 2);
-      if (rpad != nullptr)  // r also goes straight into the TF32 preconditioner's input rows
+      if (rpad != nullptr)  // r also goes straight into the TF32 preconditioner's input rows; d += a p deferred
         STLS_LAUNCH(stls::launch_cg_xr_pad(c->di, c->ri, c->pi, c->qi, N, B, eta, c->st_in, c->rw, rpad, pad_n0,
-                                           pad_np0, c->stream),
+                                           pad_np0, 1, c->stream),
                     "cg_xr");
       else
         STLS_LAUNCH(stls::launch_cg_xr<float>(c->di, c->ri, c->pi, c->qi, N, B, eta, c->st_in, c->rw, c->stream),
@@ -663,7 +663,14 @@ int solve_ir_impl(stls_ctx *c, const double *F, double *u, double tol, int maxit
       ph = phase_begin(c, 2);
       STLS_LAUNCH(stls::launch_cg_beta<float>(c->zi, c->ri, c->qi, N, B, 1, 0, c->st_in, c->rw, c->stream),
                   "cg_beta");
-      STLS_LAUNCH(stls::launch_cg_p<float>(c->zi, c->pi, N, B, 0, c->st_in, c->stream), "cg_p");
+      STLS_LAUNCH(stls::launch_cg_p<float>(c->zi, c->pi, N, B, 0, c->st_in, c->stream,
+                                           rpad != nullptr ? c->di : nullptr, c->rw.tickets),
+                  "cg_p");
+      phase_end(c, ph);
+    }
+    if (rpad != nullptr) {  // x updates deferred by the last CG updates
+      ph = phase_begin(c, 2);
+      STLS_LAUNCH(stls::launch_cg_x_pending(c->di, c->pi, N, B, c->st_in, c->stream), "cg_x_pending");
       phase_end(c, ph);
     }
     int its = 0;
