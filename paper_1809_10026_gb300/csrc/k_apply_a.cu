@@ -177,7 +177,6 @@ __device__ __forceinline__ void band_row(const T *__restrict__ band, int i, int 
 // double-float products skip the selects: their inputs are finite).
 template <typename T, int P>
 __device__ __forceinline__ void slice_body(const SliceArgs<T> &a) {
-  ptx::pdl_enter();
   constexpr int W = 2 * P + 1, D = prefetch_rows<T>(), R = D + 1;
   constexpr int RW = (kAThreads + 2 * P + 3) / 4 * 4;
   constexpr bool MASK = std::is_same<T, double>::value;
@@ -342,7 +341,6 @@ __global__ void __launch_bounds__(kAThreads, P <= 3 ? 3 : 1) slice_kernel_f64(co
 template <typename T, int P>
 __global__ void __launch_bounds__(kAThreads) zpass_kernel(const __grid_constant__ ZArgs<T> a) {
   constexpr int W = 2 * P + 1;
-  ptx::pdl_enter();
   const int tid = threadIdx.x;
   const long long col = static_cast<long long>(blockIdx.x) * kAThreads + tid;
   if (col >= a.outer * a.inner) return;  // no block-wide barrier below
@@ -429,7 +427,6 @@ __global__ void __launch_bounds__(kAThreads) zpass_kernel(const __grid_constant_
 template <typename T, int P, bool FUSE>
 __global__ void __launch_bounds__(kAThreads) tpass_kernel(const __grid_constant__ TArgs<T> a) {
   constexpr int W = 2 * P + 1;
-  ptx::pdl_enter();
   const int tid = threadIdx.x;
   const long long inner = a.inner, o = blockIdx.y;
   const long long cc = static_cast<long long>(blockIdx.x) * kAThreads + tid;
@@ -601,9 +598,9 @@ cudaError_t launch_slice_p(const SliceArgs<T> &a, cudaStream_t s) {
   if (g > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
   if (g > 0) {
     if constexpr (std::is_same<T, double>::value)
-      return launch_pdl(slice_kernel_f64<P>, dim3(static_cast<unsigned>(g)), dim3(kAThreads), 0, s, a);
+      slice_kernel_f64<P><<<static_cast<unsigned>(g), kAThreads, 0, s>>>(a);
     else
-      return launch_pdl(slice_kernel<T, P>, dim3(static_cast<unsigned>(g)), dim3(kAThreads), 0, s, a);
+      slice_kernel<T, P><<<static_cast<unsigned>(g), kAThreads, 0, s>>>(a);
   }
   return cudaGetLastError();
 }
@@ -611,7 +608,7 @@ template <typename T, int P>
 cudaError_t launch_zpass_p(const ZArgs<T> &a, cudaStream_t s) {
   const long long g = blocks_for(a.outer * a.inner);
   if (g > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-  if (g > 0) return launch_pdl(zpass_kernel<T, P>, dim3(static_cast<unsigned>(g)), dim3(kAThreads), 0, s, a);
+  if (g > 0) zpass_kernel<T, P><<<static_cast<unsigned>(g), kAThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
 template <typename T, int P>
@@ -621,9 +618,12 @@ cudaError_t launch_tpass_p(const TArgs<T> &a, cudaStream_t s) {
   if (g > 0 && a.outer > 0) {
     const dim3 grid(static_cast<unsigned>(g), static_cast<unsigned>(a.outer));
     if constexpr (std::is_same<T, float>::value) {
-      if (a.fuse.p != nullptr) return launch_pdl(tpass_kernel<T, P, true>, grid, dim3(kAThreads), 0, s, a);
+      if (a.fuse.p != nullptr) {
+        tpass_kernel<T, P, true><<<grid, kAThreads, 0, s>>>(a);
+        return cudaGetLastError();
+      }
     }
-    return launch_pdl(tpass_kernel<T, P, false>, grid, dim3(kAThreads), 0, s, a);
+    tpass_kernel<T, P, false><<<grid, kAThreads, 0, s>>>(a);
   }
   return cudaGetLastError();
 }

@@ -186,7 +186,6 @@ template <typename T, bool PAD = false, bool DEFER = false>
 __global__ void __launch_bounds__(kThreads, 8)
     cg_xr_kernel(T *__restrict__ x, T *__restrict__ r, const T *__restrict__ p,
                  const T *__restrict__ q, long long N, double tol, CGState *st, RedWork rw, PadOut pad = {}) {
-  ptx::pdl_enter();
   const int b = blockIdx.y;
   const bool active = st[b].active != 0;
   const T alpha = static_cast<T>(st[b].alpha);
@@ -243,7 +242,6 @@ __global__ void __launch_bounds__(kThreads, 8)
     cg_beta_kernel(const T *__restrict__ z, const T *__restrict__ r,
                    const T *__restrict__ q, long long N, int flexible, int first, CGState *st,
                    RedWork rw) {
-  ptx::pdl_enter();
   const int b = blockIdx.y;
   const T *zb = z + static_cast<size_t>(b) * N, *rb = r + static_cast<size_t>(b) * N;
   const T *qb = q + static_cast<size_t>(b) * N;
@@ -298,7 +296,6 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads, 8)
     cg_p_kernel(const T *__restrict__ z, T *__restrict__ p, long long N, int first,
                 CGState *st, T *__restrict__ x, unsigned *tickets) {
-  ptx::pdl_enter();
   const int b = blockIdx.y;
   if (!st[b].active) return;
   const T beta = static_cast<T>(st[b].beta);
@@ -338,7 +335,6 @@ __global__ void __launch_bounds__(kThreads, 8)
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 8)
     cg_x_pending_kernel(T *__restrict__ x, const T *__restrict__ p, long long N, const CGState *st) {
-  ptx::pdl_enter();
   const int b = blockIdx.y;
   if (!st[b].xpend) return;
   const T alpha = static_cast<T>(st[b].alpha);
@@ -574,18 +570,18 @@ cudaError_t launch_cg_xr(T *x, T *r, const T *p, const T *q, long long N, int B,
 template <typename T>
 cudaError_t launch_cg_beta(const T *z, const T *r, const T *q, long long N, int B, int flexible, int first,
                            CGState *st, RedWork rw, cudaStream_t s) {
-  return launch_pdl(cg_beta_kernel<T>, dim3(rw.grid, B), dim3(kThreads), 0, s, z, r, q, N, flexible, first, st, rw);
+  cg_beta_kernel<T><<<dim3(rw.grid, B), kThreads, 0, s>>>(z, r, q, N, flexible, first, st, rw);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_cg_p(const T *z, T *p, long long N, int B, int first, CGState *st, cudaStream_t s, T *x,
                         unsigned *tickets) {
   if (x != nullptr && tickets == nullptr) return cudaErrorInvalidValue;
-  return launch_pdl(cg_p_kernel<T>, dim3(grid_1d(N), B), dim3(kThreads), 0, s, z, p, N, first, st, x, tickets);
+  cg_p_kernel<T><<<dim3(grid_1d(N), B), kThreads, 0, s>>>(z, p, N, first, st, x, tickets);
   return cudaGetLastError();
 }
 cudaError_t launch_cg_x_pending(float *x, const float *p, long long N, int B, const CGState *st, cudaStream_t s) {
-  return launch_pdl(cg_x_pending_kernel<float>, dim3(grid_1d(N), B), dim3(kThreads), 0, s, x, p, N, st);
+  cg_x_pending_kernel<float><<<dim3(grid_1d(N), B), kThreads, 0, s>>>(x, p, N, st);
   return cudaGetLastError();
 }
 #define STLS_INST(T)                                                                                       \
@@ -606,9 +602,9 @@ cudaError_t launch_cg_xr_pad(float *x, float *r, const float *p, const float *q,
     return cudaErrorInvalidValue;
   PadOut pad{rpad, n0, np0};
   if (defer)
-    return launch_pdl(cg_xr_kernel<float, true, true>, dim3(rw.grid, B), dim3(kThreads), 0, s, x, r, p, q, N, tol,
-                      st, rw, pad);
-  cg_xr_kernel<float, true><<<dim3(rw.grid, B), kThreads, 0, s>>>(x, r, p, q, N, tol, st, rw, pad);
+    cg_xr_kernel<float, true, true><<<dim3(rw.grid, B), kThreads, 0, s>>>(x, r, p, q, N, tol, st, rw, pad);
+  else
+    cg_xr_kernel<float, true><<<dim3(rw.grid, B), kThreads, 0, s>>>(x, r, p, q, N, tol, st, rw, pad);
   return cudaGetLastError();
 }
 cudaError_t launch_ir_start(const double *r64, float *r32, float *d, long long N, int B, const CGState *outer,

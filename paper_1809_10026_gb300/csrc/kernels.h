@@ -9,25 +9,6 @@
 
 namespace stls {
 
-// Launch with programmatic stream serialization: the kernel (which starts with
-// ptx::pdl_enter) may begin launching while the previous kernel in the stream
-// finishes.
-template <typename... KArgs, typename... Args>
-cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
-                       Args &&...args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = block;
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args &&>(args)...);
-}
-
 // A tensor seen along one mode: (outer, n, inner), inner fastest.  Entry
 // (o, i, c) of the input lives at base + o * in_outer_stride + i * inner + c.
 struct ModeView {

@@ -341,15 +341,6 @@ __host__ __device__ inline uint32_t idesc_bf16(int M, int N, int b_mn_major) {
   return d;
 }
 
-// Programmatic dependent launch, at the start of a kernel: allow the next
-// kernel in the stream to begin launching, then wait until the previous one
-// has completed and its memory is visible.  Nothing may touch global memory
-// before this.  Both are no-ops for a kernel launched without the attribute.
-__device__ __forceinline__ void pdl_enter() {
-  asm volatile("griddepcontrol.launch_dependents;");
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-}
-
 // Instruction descriptor of kind::tf32 with TF32 A and B (both K-major), FP32 D.
 __host__ __device__ inline uint32_t idesc_tf32(int M, int N) {
   uint32_t d = 0;
