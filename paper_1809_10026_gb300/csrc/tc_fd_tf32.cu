@@ -18,8 +18,10 @@
 //
 // Rounding.  Every stored intermediate is rounded to TF32 (round to nearest,
 // ties away: cvt.rna), so the MMA, which reads the top 19 bits of each FP32
-// operand, uses it exactly; the first pass reads r through a padding kernel
-// that rounds the same way, and the last pass writes z unrounded.  The
+// operand, uses it exactly; the first pass reads r in the same padded,
+// rounded rows, written either by a padding kernel or directly by the
+// producer of r (tc_fd_rot_padded_input: the inner CG updates of the
+// refinement form), and the last pass writes z unrounded.  The
 // division by lambda_t[m] + lambda_s[c] (step 3) is fused into the epilogue of
 // the forward time pass, whose fibers are the colexicographic spatial indices
 // c; FP32 (__fdividef), from the FP64 eigenvalues rounded once.
