@@ -11,6 +11,19 @@
 
 namespace stls {
 
+// Raises (never lowers) a kernel's dynamic shared-memory limit.  The limit is
+// per kernel and per process, so contexts of different sizes share it: a
+// smaller context created later must not lower the limit a larger one needs.
+template <typename K>
+cudaError_t raise_smem_limit(K *kernel, int bytes) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, reinterpret_cast<const void *>(kernel));
+  if (e != cudaSuccess) return e;
+  if (fa.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
+  return cudaFuncSetAttribute(reinterpret_cast<const void *>(kernel), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              bytes);
+}
+
 struct FusedFd;
 struct RotFd;
 

@@ -850,7 +850,7 @@ cudaError_t plan_slab(SlabPlan &pl, SlabArgs base, long long nsl, int sms) {
       pl.smem = smem;
       const long long nsteps = (nsl + G - 1) / G;
       pl.grid = static_cast<int>(std::min<long long>(nsteps, sms));
-      return cudaFuncSetAttribute(slab_kernel<InT, OutT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      return raise_smem_limit(slab_kernel<InT, OutT>, smem);
     }
   }
   return cudaErrorInvalidConfiguration;
@@ -915,7 +915,7 @@ cudaError_t plan_stream(StreamPlan &pl, int n, long long cols, long long outer, 
   }
   const long long ntiles = outer * s.nct;
   pl.grid = static_cast<int>(std::min<long long>(ntiles, static_cast<long long>(sms) * ctas_per_sm(pl.smem)));
-  return cudaFuncSetAttribute(stream_kernel<TIME>, cudaFuncAttributeMaxDynamicSharedMemorySize, pl.smem);
+  return raise_smem_limit(stream_kernel<TIME>, pl.smem);
 }
 
 }  // namespace

@@ -462,9 +462,8 @@ cudaError_t tc_fd_rot_create(RotFd *&out, std::vector<void *> &allocs, int d, co
                          return x.smem < y.smem;
                        })->smem;
   const int sm = static_cast<int>(maxsm);
-  if ((e = cudaFuncSetAttribute(rot_kernel<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) ||
-      (e = cudaFuncSetAttribute(rot_kernel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) ||
-      (e = cudaFuncSetAttribute(rot_kernel<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)))
+  if ((e = raise_smem_limit(rot_kernel<float, false>, sm)) || (e = raise_smem_limit(rot_kernel<float, true>, sm)) ||
+      (e = raise_smem_limit(rot_kernel<double, false>, sm)))
     return e;
   return cudaSuccess;
 }

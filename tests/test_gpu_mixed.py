@@ -189,3 +189,21 @@ def test_refinement_batch_matches_direct_solve():
         ref = direct_solve(A, F[b])
         assert info[b]["status"] == "ok"
         assert np.linalg.norm(u[b] - ref) / np.linalg.norm(ref) <= 1e-10
+
+
+@pytest.mark.parametrize("form", ["bf16", "tf32"])
+def test_contexts_of_different_sizes_coexist(form):
+    """The tensor-core kernels' dynamic shared-memory limits are per kernel and
+    per process: a small context created after a large one must leave the large
+    one working, with the same result."""
+    big = _solver(3, 3, 24, precision=form)
+    r = _cuda_arr(synth.uniform(big.N, 21))
+    z1 = big.apply_precond(r).cpu().numpy()
+    small = _solver(2, 2, 3, precision=form)
+    small.apply_precond(_cuda_arr(synth.uniform(small.N, 22)))
+    z2 = big.apply_precond(r).cpu().numpy()
+    assert np.array_equal(z1, z2)
+
+
+def _cuda_arr(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
