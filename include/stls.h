@@ -103,7 +103,9 @@ typedef struct {
  * the generalized eigendecompositions of Algorithm 1, step 1, on the host in
  * FP64, uploads them and allocates the workspace for `batch` right-hand
  * sides.  `cuda_stream` is a cudaStream_t (NULL = legacy default stream).
- * On failure *out is NULL and the return code says why. */
+ * On failure *out is NULL and the return code says why.  Calls on one
+ * context must not overlap (one host thread at a time); contexts of any
+ * sizes may coexist in a process and be used one after another. */
 int stls_create(stls_ctx **out, const stls_params *prm, void *cuda_stream);
 
 /* Release everything the context owns.  NULL is accepted. */
