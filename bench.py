@@ -46,7 +46,9 @@ WORKLOAD = dict(name="cube3d_p3_n64", d=3, p=3, n_el=64, T=1.0, tol=1e-8, tag=4,
 # baseline extrapolates one oracle iteration by this count)
 FP64_ITERS = 17
 PAPER_DOFS = 18125250 / 227.93  # Table 1, p = 3, n_sub = 64: serial Matlab, i7-5820K (context)
-METRIC = "PCG solve DoF/s at relative residual 1e-8 (mixed BF16 form vs FP64 form)"
+# The line carries the DoF/s (value), the solve time (ms_per_step), the mixed
+# forms beside the FP64 one (forms) and the preconditioner's roofline
+METRIC = "PCG DoF/s & solve time, mixed vs FP64 at 1e-8 residual; precond apply %roofline"
 # form name -> (precision, refine, every outer residual in FP64); the "_ir"
 # forms take provisional double-float outer residuals before the last one,
 # the "_ir64" forms take every outer residual in FP64

@@ -62,3 +62,26 @@ def test_replica_rate_single_gpu():
     sys.path.insert(0, ROOT)
     import bench
     assert bench.replica_rate(18125250, 5, 1, 1000.0) == pytest.approx(18125250 * 5)
+
+
+def test_reference_arm_json_line(capsys, monkeypatch):
+    """The reference arm (the oracle's FP64 PCG on the host) prints one JSON
+    line with the keys of the bench contract; run here on a small cube."""
+    import json
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.delenv("RANK", raising=False)
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    monkeypatch.setattr(bench, "WORKLOAD", dict(bench.WORKLOAD, n_el=4, name="cube3d_p3_n4"))
+    bench.run_reference(argparse.Namespace(steps=2, warmup=1))
+    out = capsys.readouterr().out.strip().splitlines()
+    assert len(out) == 1
+    line = json.loads(out[0])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == "DoF/s"
+    assert line["value"] > 0 and line["higher_is_better"] is True and line["n_gpus"] == 1
+    assert line["steps"] == 2 and line["warmup"] == 1 and line["dtype"] == "f64"
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] >= 1 and cb["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": "DoF/s", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    assert line["config"]["workload"] == "cube3d_p3_n4"
