@@ -2,14 +2,15 @@
 """Benchmark: PCG solve of the space-time least-squares heat-equation system.
 
 One step = one complete solve A u = F from u = 0 to ||r|| / ||F|| <= 1e-8
-(preconditioner setup excluded; it runs once per context) on the workload
+(context setup excluded: it runs once per context and is reported as
+setup_ms) on the workload
 "cube3d_p3_n64": (0,1)^3 x (0,1), degree 3 splines, 64 elements per
 direction, N = 18,125,250 unknowns, F ~ U[-1,1] (seed 1809100264).
 
 Metric: solved degrees of freedom per second (DoF/s), whole job.  The
 headline form is the mixed one of this workload: TF32 tensor-core
 preconditioner apply with FP32 accumulation, FP64 outer residual F - A u
-(iterative refinement around a flexible CG in FP32 with FP64-accumulated inner
+(iterative refinement around a flexible CG in FP32 with compensated inner
 products; the outer steps before the last take a provisional residual with
 the double-float A x).  The other forms are measured on the same workload in
 the same run and reported under "forms": the same with every outer residual
@@ -256,9 +257,11 @@ def roofline_entry(phase, ms, count, S, p, peaks, refine):
 def run_form(stls, name, W, F, args, world, sampler=None):
     import torch
     precision, refine, fp64_res = FORMS[name]
+    t0 = time.perf_counter()
     S = stls.Solver(W["d"], W["p"], W["n_el"], W["T"], precision=precision, refine=refine,
                     fp64_residuals=fp64_res,
                     device=F.device)
+    setup_ms = (time.perf_counter() - t0) * 1e3  # host eigendecompositions, uploads, workspace
     u = torch.empty_like(F)
     steps = args.steps if sampler is not None else max(1, min(args.steps, args.form_steps))
     if sampler is not None:
@@ -268,7 +271,7 @@ def run_form(stls, name, W, F, args, world, sampler=None):
     ms_max = max_over_ranks(ms, world, F.device)
     _, _, _, phases = timed_solves(S, F, u, W["tol"], 1, 0, world, True)
     return dict(S=S, u=u, ms=ms_max, infos=infos, launches=launches, phases=phases, steps=steps,
-                clocks=clocks, precision=precision, refine=refine)
+                clocks=clocks, precision=precision, refine=refine, setup_ms=setup_ms)
 
 
 def cpu_baseline_sample(F, iters):
@@ -367,6 +370,9 @@ def run_ours(args):
         "precond_roofline": entries.get("precond"),
         "phase_ms_per_solve": {k: v[0] for k, v in ph.items()},
         "phase_calls_per_solve": {k: v[1] for k, v in ph.items()},
+        # context creation (not in value): 1D matrices and eigendecompositions on
+        # the host, uploads, workspace, tensor-core operand images
+        "setup_ms": main["setup_ms"],
         "e2e": {"value": replica_rate(N, main["steps"], world, e2e_s * 1e3), "unit": "DoF/s",
                 "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N},
         "gpu_launches": main["launches"],
@@ -383,6 +389,7 @@ def run_ours(args):
                        "ms_per_step": r["ms"] / r["steps"], "steps": r["steps"],
                        "iterations": r["infos"][-1]["iters"], "outer": r["infos"][-1]["outer"],
                        "true_rel_res": r["infos"][-1]["true_rel_res"], "gpu_launches": r["launches"],
+                       "setup_ms": r["setup_ms"],
                        "phase_ms_per_solve": {k: v[0] for k, v in phx.items()},
                        "rooflines": {k: roofline_entry(k, v[0], v[1], Sx, p, peaks, r["refine"])
                                      for k, v in phx.items() if v[1]}}

@@ -523,10 +523,12 @@ int solve_impl(stls_ctx *c, const double *F, double *u, double tol, int maxit, s
 }
 
 // Iterative refinement (mixed forms, refine = 1).  Outer loop in FP64:
-// r = F - A u (FP64 A x), stop when ||r|| / ||F|| <= tol; otherwise solve
-// A d = r / ||r|| approximately by flexible CG in FP32 (FP32 vectors and A p,
-// the tensor-core preconditioner, inner products accumulated in FP64) until
-// its residual falls below inner_tol, and update u += ||r|| d in FP64.
+// r = F - A u (FP64 A x; provisional steps in double-float), stop when
+// ||r|| / ||F|| <= tol; otherwise solve A d = r 2^-k (||r|| = f 2^k, f in
+// [0.5, 1): an exact scaling) approximately by flexible CG in FP32 (FP32
+// vectors and A p, the tensor-core preconditioner, inner products compensated
+// in FP32 per thread and summed in FP64) until its residual falls below the
+// inner tolerance, and update u += 2^k d in FP64.
 int solve_ir_impl(stls_ctx *c, const double *F, double *u, double tol, int maxit, stls_solve_info *info) {
   if (!(tol >= 0.0) || maxit < 0) return set_err(c, STLS_EINVAL, "tol must be >= 0 and maxit >= 0");
   if (check_ptr(c, F, "F") || check_ptr(c, u, "u")) return STLS_EINVAL;
@@ -607,7 +609,7 @@ int solve_ir_impl(stls_ctx *c, const double *F, double *u, double tol, int maxit
         eta = std::min(0.1, std::max(eta_min, std::pow(R, 1.0 / K)));
       }
     }
-    // ---- inner flexible CG in FP32 on A d = r / ||r|| ----
+    // ---- inner flexible CG in FP32 on A d = r 2^-k ----
     ph = phase_begin(c, 2);
     STLS_LAUNCH(stls::launch_ir_start(r64, c->ri, c->di, N, B, c->st, c->st_in, c->rw, rpad, pad_n0, pad_np0,
                                       c->stream),
