@@ -1,6 +1,6 @@
 """Differentiable solve with a lifted initial datum (Sec. 3.1) on the GPU.
 
-cfg 5: d = 2, p = 3, 48 elements (120,050 unknowns per right-hand side),
+Workload square2d_p3_n48_b16: d = 2, p = 3, 48 elements (120,050 unknowns per right-hand side),
 16 right-hand sides per launch, loss 0.5 ||u - u_target||^2.  Gradients of
 the hand-written backward (adjoint solve + lifting transpose) are checked
 against central finite differences of the GPU forward solve (h = 1e-6, 20
@@ -64,7 +64,7 @@ def test_gradient_matches_oracle_reduced_mesh():
         assert np.linalg.norm(dc0[b] - dc0r) <= 1e-8 * np.linalg.norm(dc0r)
 
 
-def test_cfg5_gradients_full_size():
+def test_gradients_square2d_p3_n48_b16():
     import paper_1809_10026_gb300 as stls
     prob = STProblem(2, 3, 48)
     B = 16

@@ -66,11 +66,11 @@ CASES = [dict(d=2, p=2, n_el=7), dict(d=2, p=3, n_el=9, T=1.3), dict(d=2, p=5, n
          dict(d=2, p=3, n_el=[40, 7])]
 
 
-@pytest.mark.parametrize("cfg", CASES, ids=lambda c: "-".join(f"{k}{v}" for k, v in c.items()))
-def test_apply_A_df_matches_oracle(cfg):
-    kw = {k: cfg[k] for k in ("T", "p_t", "n_el_t") if k in cfg}
-    prob = STProblem(cfg["d"], cfg["p"], cfg["n_el"], **kw)
-    S = _solver(cfg["d"], cfg["p"], cfg["n_el"], precision="bf16", refine=True, batch=2, **kw)
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "-".join(f"{k}{v}" for k, v in c.items()))
+def test_apply_A_df_matches_oracle(case):
+    kw = {k: case[k] for k in ("T", "p_t", "n_el_t") if k in case}
+    prob = STProblem(case["d"], case["p"], case["n_el"], **kw)
+    S = _solver(case["d"], case["p"], case["n_el"], precision="bf16", refine=True, batch=2, **kw)
     x = synth.uniform(prob.N, 41, batch=2).reshape(2, prob.N)
     x[1] *= 3.0e5  # a second magnitude: the FP32 parts scale with it
     y = S.apply_A_df(_cuda(x)).cpu().numpy().reshape(2, prob.N)
@@ -110,7 +110,7 @@ def test_apply_A_df_zero_and_exact_values():
     assert np.all(np.abs(y - ref) <= BOUND * B)
 
 
-def test_cfg4_df_residual_accuracy():
+def test_df_residual_accuracy_cube3d_p3_n64():
     """3D, p = 3, 64 elements (18,125,250 DoF).  (1) Random x: the double-float
     product agrees with the FP64 one normwise to 1e-12.  (2) The solution of a
     refinement solve: F - A_df u differs from the FP64 residual F - A u by

@@ -114,7 +114,7 @@ def test_tc_precond_anisotropic_matches_model(form, d, p, n_el, kw, batch):
 
 
 @pytest.mark.parametrize("form", ["bf16", "tf32"])
-def test_tc_precond_full_size_cfg4(form):
+def test_tc_precond_cube3d_p3_n64(form):
     prob = STProblem(3, 3, 64)
     fd = FD(prob)
     S = _solver(3, 3, 64, precision=form)
@@ -124,7 +124,7 @@ def test_tc_precond_full_size_cfg4(form):
 
 
 @pytest.mark.parametrize("form", ["bf16", "tf32"])
-def test_mixed_solve_cfg3(form):
+def test_mixed_solve_cube3d_p4_n32(form):
     """3D, p = 4, 32 elements (1,375,640 DoF), manufactured load: flexible CG with the
     tensor-core preconditioner reaches the FP64 solution."""
     pi = np.pi
@@ -144,7 +144,7 @@ def test_mixed_solve_cfg3(form):
     print(form, "iters@1e-8", i8[0]["iters"], "iters@1e-12", i12[0]["iters"], "fp64 iters@1e-12", i64[0]["iters"])
 
 
-def test_mixed_solve_cfg4_bf16():
+def test_mixed_solve_cube3d_p3_n64_bf16():
     prob_N = 18125250
     S = _solver(3, 3, 64, precision="bf16")
     F = torch.from_numpy(synth.uniform(prob_N, 4)).cuda()
@@ -154,7 +154,7 @@ def test_mixed_solve_cfg4_bf16():
 
 
 @pytest.mark.parametrize("form", ["bf16", "tf32"])
-def test_refinement_solve_cfg3(form):
+def test_refinement_solve_cube3d_p4_n32(form):
     """Iterative refinement: FP64 residual F - A u, inner FP32 flexible CG with the
     tensor-core preconditioner; the stopping test is on the true FP64 residual."""
     pi = np.pi

@@ -69,11 +69,11 @@ EDGE = [dict(d=2, p=2, n_el=1, T=1.0), dict(d=3, p=2, n_el=2, T=0.8),
         dict(d=2, p=2, n_el=[6, 9], T=0.5, p_t=5, n_el_t=3)]
 
 
-@pytest.mark.parametrize("cfg", EDGE, ids=lambda c: "-".join(f"{k}{v}" for k, v in c.items()))
-def test_apply_A_edge_cases(cfg):
-    kw = {k: cfg[k] for k in ("p_t", "n_el_t") if k in cfg}
-    prob = STProblem(cfg["d"], cfg["p"], cfg["n_el"], cfg["T"], **kw)
-    S = _solver(cfg["d"], cfg["p"], cfg["n_el"], cfg["T"], batch=2, **kw)
+@pytest.mark.parametrize("case", EDGE, ids=lambda c: "-".join(f"{k}{v}" for k, v in c.items()))
+def test_apply_A_edge_cases(case):
+    kw = {k: case[k] for k in ("p_t", "n_el_t") if k in case}
+    prob = STProblem(case["d"], case["p"], case["n_el"], case["T"], **kw)
+    S = _solver(case["d"], case["p"], case["n_el"], case["T"], batch=2, **kw)
     x = synth.uniform(prob.N, 31, batch=2).reshape(2, prob.N)
     y = S.apply_A(_cuda(x)).cpu().numpy().reshape(2, prob.N)
     A = prob.assemble_A_kron()
@@ -117,15 +117,15 @@ def test_apply_precond_in_place():
     np.testing.assert_allclose(x.cpu().numpy(), ref, rtol=0, atol=fd_tolerance(fd) * np.abs(ref).max())
 
 
-def _cfg1_terms():
+def _line1d_terms():
     return [(PI, lambda t: np.cos(PI * t), [lambda x: np.sin(PI * x)]),
             (PI ** 2, lambda t: np.sin(PI * t), [lambda x: np.sin(PI * x)])]
 
 
-def test_solve_cfg1_matches_direct_solve():
+def test_solve_line1d_p2_n16_matches_direct_solve():
     """1D space + time, p = 2, 16 elements, u = sin(pi x) sin(pi t), tol 1e-10 and 1e-13."""
     prob = STProblem(1, 2, 16)
-    F = prob.load_separable(_cfg1_terms())
+    F = prob.load_separable(_line1d_terms())
     u_ref = direct_solve(prob.assemble_A_kron(), F)
     S = _solver(1, 2, 16)
     for tol, bound in [(1e-13, 1e-10), (1e-10, 1e-8)]:
@@ -201,7 +201,7 @@ def test_table1_iterations_on_gpu(n_sub, p):
     assert info[0]["true_rel_res"] <= 2e-8
 
 
-def test_cfg2_full_size_solve():
+def test_square2d_p3_n64_full_size_solve():
     """2D space + time, p = 3, 64 elements (278,850 DoF), perturbed manufactured load, tol 1e-10."""
     prob = STProblem(2, 3, 64)
     s = lambda x: np.sin(PI * x)
@@ -219,7 +219,7 @@ def test_cfg2_full_size_solve():
     assert np.linalg.norm(u13.cpu().numpy() - u_ref) / np.linalg.norm(u_ref) <= 1e-10
 
 
-def test_cfg4_full_size_operators_sampled():
+def test_cube3d_p3_n64_operators_sampled():
     """3D, p = 3, 64 elements (18,125,250 DoF): A x on sampled rows, P^{-1} r in full."""
     prob = STProblem(3, 3, 64)
     S = _solver(3, 3, 64)
