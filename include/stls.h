@@ -71,8 +71,8 @@ typedef struct {
                        an outer loop computes the residual r = F - A u in FP64
                        and corrects u with an inner flexible CG in FP32
                        (FP32 vectors and A p, tensor-core preconditioner, inner
-                       products accumulated in FP64) that reduces its scaled
-                       residual by inner_tol.  With d = 2, 3 an outer step whose
+                       products compensated in FP32 per thread and summed in
+                       FP64) that reduces its scaled residual by inner_tol.  With d = 2, 3 an outer step whose
                        predicted residual ||r|| max(inner residual, 4e-4) exceeds
                        both 100 tol and 1e-8 takes a provisional residual with
                        the double-float A x (stls_apply_A_df); the FP64 residual

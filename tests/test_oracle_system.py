@@ -111,6 +111,25 @@ def test_convergence_rates(p, norm, rate):
     assert abs(observed - rate) < 0.35, (errs, observed)
 
 
+@pytest.mark.parametrize("p_t", [2, 3])
+def test_unbalanced_degrees_gain_one_order(p_t):
+    """Spatial degree p_s = p_t + 1: the V0 error converges as h^(p_t), one
+    order above the h^(p_t - 1) of p_s = p_t (Sec. 5.1, unbalanced degrees)."""
+    terms, exact = sin_solution_1d()
+
+    def v0_rate(p_s):
+        errs = []
+        for n in (8, 16, 32):
+            prob = STProblem(1, p_s, n, 1.0, p_t=p_t)
+            u = direct_solve(prob.assemble_A_kron(), prob.load_separable(terms))
+            errs.append(errors(prob, u, exact)["V0"])
+        return np.log2(errs[-2] / errs[-1])
+
+    unbalanced, balanced = v0_rate(p_t + 1), v0_rate(p_t)
+    assert abs(unbalanced - p_t) < 0.35, unbalanced
+    assert abs(balanced - (p_t - 1)) < 0.35, balanced
+
+
 @pytest.mark.parametrize("d,p,n_el", [(1, 2, 5), (2, 3, 4), (3, 2, 3)])
 def test_sampled_rows_of_A(d, p, n_el):
     from oracle.system import apply_A_rows
