@@ -1,0 +1,62 @@
+"""CPU checks of bench.py's roofline bookkeeping: the entry of each timed
+operation carries the keys of the bench line's roofline object, its achieved
+rate follows from the operation's algorithmic bytes or flops and the measured
+time, and frac = achieved / peak.  No GPU needed."""
+import os
+import sys
+import types
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+N = 18125250
+PEAKS = {"hbm_gbs": 6774.0, "bf16_tflops": 1891.0, "bf16_tflops_sustained": 1700.0, "source": "measured"}
+
+
+def fake_solver(precision):
+    # 3D, p = 3, 64 elements: 65 unknowns per spatial direction, 66 in time
+    return types.SimpleNamespace(precision=precision, N=N, n_s=[65, 65, 65], n_t=66, d=3)
+
+
+def test_flop_counts_of_the_workload():
+    S = fake_solver("fp64")
+    # 15 banded products of 2(2p+1) flops per unknown (p = 3)
+    assert bench.apply_A_flops(S, 3) == pytest.approx(15 * 14 * N)
+    # Algorithm 1: 4 N (sum of the 1D sizes) + N
+    assert bench.fd_flops(S) == pytest.approx(4.0 * N * (3 * 65 + 66) + N)
+
+
+@pytest.mark.parametrize("phase,precision,refine,bound,unit", [
+    ("precond", "tf32", True, "hbm", "GB/s"),
+    ("precond", "bf16", False, "hbm", "GB/s"),
+    ("precond", "fp64", False, "alu", "TFLOP/s"),
+    ("apply_A", "tf32", True, "alu", "TFLOP/s"),
+    ("apply_A_f32", "tf32", True, "alu", "TFLOP/s"),
+    ("apply_A_df", "tf32", True, "alu", "Top/s"),
+])
+def test_roofline_entry_keys_and_rate(phase, precision, refine, bound, unit):
+    S = fake_solver(precision)
+    ms, count = 5.0, 19  # ms over all calls of the operation in one solve, calls
+    e = bench.roofline_entry(phase, ms, count, S, 3, PEAKS, refine)
+    for k in ("bound", "achieved", "peak", "unit", "frac", "traffic"):
+        assert k in e
+    assert e["bound"] == bound and e["unit"] == unit
+    assert e["frac"] == pytest.approx(e["achieved"] / e["peak"])
+    per_s = ms / count * 1e-3
+    if phase == "precond" and precision != "fp64":
+        nbytes = (8.0 if refine else 16.0) * N
+        assert e["achieved"] == pytest.approx(nbytes / per_s / 1e9)
+        assert e["peak"] == PEAKS["hbm_gbs"]
+    if phase == "apply_A_f32":
+        assert e["achieved"] == pytest.approx(bench.apply_A_flops(S, 3) / per_s / 1e12)
+    if (phase, precision, refine) in bench.TRAFFIC:
+        assert e["traffic"] == bench.TRAFFIC[(phase, precision, refine)]
+    else:
+        assert e["traffic"] is None
+
+
+def test_roofline_entry_without_calls_is_none():
+    assert bench.roofline_entry("precond", 0.0, 0, fake_solver("tf32"), 3, PEAKS, True) is None
