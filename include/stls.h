@@ -174,6 +174,17 @@ int stls_solve_host(stls_ctx *ctx, const double *F_host, double *u_host, double 
  * c0: device, B x N_s; y: device, B x N. */
 int stls_apply_lift(stls_ctx *ctx, const double *c0, double *y);
 
+/* Right-hand side of the lifted problem: rhs = F - G c0 (G as for
+ * stls_apply_lift).  F, rhs: device, B x N; c0: device, B x N_s; rhs must
+ * not overlap F or c0.  Uses the context's workspace (stream-ordered like
+ * every call on the context). */
+int stls_lifted_rhs(stls_ctx *ctx, const double *F, const double *c0, double *rhs);
+
+/* Solution of the lifted problem from its correction: u = w + 1_{n_t} x c0,
+ * i.e. u[b, t, :] = w[b, t, :] + c0[b, :] for every time index t.
+ * w, u: device, B x N; c0: device, B x N_s; u must not overlap w or c0. */
+int stls_lift_add(stls_ctx *ctx, const double *w, const double *c0, double *u);
+
 /* Adjoint of the lifted solve for a loss L(u): given g = dL/du and
  * lam = A^{-1} g, writes dc0 = sum_t g[t, :] - G^T lam (device, B x N_s). */
 int stls_lift_adjoint(stls_ctx *ctx, const double *g, const double *lam, double *dc0);

@@ -175,6 +175,24 @@ class Solver:
         _check(self.lib.stls_apply_lift(self.ctx, self._ptr(c0), self._ptr(y)), self.ctx)
         return y
 
+    def lifted_rhs(self, F, c0):
+        """F - G c0: the right-hand side of the problem with initial datum c0."""
+        F = self._vec(F, self.N, "F")
+        c0 = self._vec(c0, self.N_s, "c0")
+        rhs = self._out(F.shape, self.N)
+        self._stream()
+        _check(self.lib.stls_lifted_rhs(self.ctx, self._ptr(F), self._ptr(c0), self._ptr(rhs)), self.ctx)
+        return rhs
+
+    def lift_add(self, w, c0):
+        """u = w + 1_{n_t} x c0: the solution of the lifted problem from its correction w."""
+        w = self._vec(w, self.N, "w")
+        c0 = self._vec(c0, self.N_s, "c0")
+        u = self._out(w.shape, self.N)
+        self._stream()
+        _check(self.lib.stls_lift_add(self.ctx, self._ptr(w), self._ptr(c0), self._ptr(u)), self.ctx)
+        return u
+
     def lift_adjoint(self, g, lam):
         g = self._vec(g, self.N, "g")
         lam = self._vec(lam, self.N, "lam")

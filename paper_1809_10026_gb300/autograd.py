@@ -11,16 +11,14 @@ import torch
 class SolveFn(torch.autograd.Function):
     @staticmethod
     def forward(ctx, F, c0, solver, tol, maxit):
-        rhs = F - solver.apply_lift(c0) if c0 is not None else F
+        rhs = solver.lifted_rhs(F, c0) if c0 is not None else F
         w, info = solver.solve(rhs.contiguous(), tol, maxit)
         ctx.solver, ctx.tol, ctx.maxit = solver, tol, maxit
         ctx.has_c0 = c0 is not None
         ctx.info = info
         if c0 is None:
             return w
-        B = solver.batch
-        u = w.view(B, solver.n_t, solver.N_s) + c0.view(B, 1, solver.N_s)
-        return u.reshape(w.shape)
+        return solver.lift_add(w, c0)
 
     @staticmethod
     def backward(ctx, g):

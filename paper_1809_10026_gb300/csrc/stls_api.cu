@@ -51,6 +51,7 @@ struct stls_ctx {
   double *Uf[4] = {}, *Ub[4] = {};  // U^T (forward) and U (backward), row-major
   double *lam_t = nullptr, *lam_s = nullptr;
   double *e_end = nullptr, *m_int = nullptr;
+  double *ones_t = nullptr, *zeros_t = nullptr;  // n_t ones and zeros (u = w + 1 x c0)
   // workspace
   double *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr;
   double *fd_tmp[2] = {};
@@ -827,6 +828,8 @@ int stls_create(stls_ctx **out, const stls_params *prm, void *cuda_stream) {
   if (!rc) rc = upload(c, &c->lam_t, c->hs.eig_t.lam);
   if (!rc) rc = upload(c, &c->e_end, Tm.end_values);
   if (!rc) rc = upload(c, &c->m_int, Tm.integrals);
+  if (!rc) rc = upload(c, &c->ones_t, std::vector<double>(Tm.n, 1.0));
+  if (!rc) rc = upload(c, &c->zeros_t, std::vector<double>(Tm.n, 0.0));
   if (!rc) {
     // lambda_s[c] = sum_k lambda_k[i_k(c)] over the colexicographic spatial index
     std::vector<double> ls(c->Ns, 0.0);
@@ -989,6 +992,29 @@ int stls_apply_lift(stls_ctx *c, const double *c0, double *y) {
   if (rc) return rc;
   STLS_LAUNCH(stls::launch_lift_combine(Ls, Js, c->e_end, c->m_int, y, c->Ns, c->n_t, c->B, c->stream),
               "lift_combine");
+  return STLS_OK;
+}
+
+int stls_lifted_rhs(stls_ctx *c, const double *F, const double *c0, double *rhs) {
+  if (c == nullptr) return STLS_EINVAL;
+  if (check_ptr(c, F, "F") || check_ptr(c, c0, "c0") || check_ptr(c, rhs, "rhs")) return STLS_EINVAL;
+  if (rhs == F || rhs == c0) return set_err(c, STLS_EINVAL, "lifted_rhs: rhs must not overlap F or c0");
+  double *Gc0 = c->fd_tmp[0];  // B x N workspace
+  int rc = stls_apply_lift(c, c0, Gc0);
+  if (rc) return rc;
+  STLS_LAUNCH(stls::launch_axpy(F, Gc0, -1.0, rhs, static_cast<long long>(c->B) * c->N, c->stream), "axpy");
+  return STLS_OK;
+}
+
+int stls_lift_add(stls_ctx *c, const double *w, const double *c0, double *u) {
+  if (c == nullptr) return STLS_EINVAL;
+  if (check_ptr(c, w, "w") || check_ptr(c, c0, "c0") || check_ptr(c, u, "u")) return STLS_EINVAL;
+  if (u == w || u == c0) return set_err(c, STLS_EINVAL, "lift_add: u must not overlap w or c0");
+  // 1_{n_t} x c0 (+ 0 x c0) into the B x N workspace, then u = w + it
+  double *y = c->fd_tmp[0];
+  STLS_LAUNCH(stls::launch_lift_combine(c0, c0, c->ones_t, c->zeros_t, y, c->Ns, c->n_t, c->B, c->stream),
+              "lift_combine");
+  STLS_LAUNCH(stls::launch_axpy(w, y, 1.0, u, static_cast<long long>(c->B) * c->N, c->stream), "axpy");
   return STLS_OK;
 }
 

@@ -95,3 +95,32 @@ def test_gradients_square2d_p3_n48_b16():
         assert np.linalg.norm(u[b] - ur) <= 1e-9 * np.linalg.norm(ur)
         assert np.linalg.norm(dF[b] - lam) <= 1e-8 * np.linalg.norm(lam)
         assert np.linalg.norm(dc0[b] - dc0r) <= 1e-8 * np.linalg.norm(dc0r)
+
+
+@pytest.mark.parametrize("d,p,n_el,T", [(1, 2, 9, 1.0), (2, 3, 6, 0.7), (3, 2, 3, 1.4)])
+def test_lift_calls_match_oracle(d, p, n_el, T):
+    """stls_lifted_rhs = F - G c0 and stls_lift_add = w + 1_{n_t} x c0 (Sec. 3.1
+    lifting), two right-hand sides, against the oracle's G; the addition is
+    one rounding per entry, so it is compared exactly."""
+    import paper_1809_10026_gb300 as stls
+    prob = STProblem(d, p, n_el, T)
+    B = 2
+    S = stls.Solver(d, p, n_el, T, batch=B)
+    rng = np.random.default_rng(7)
+    F = rng.standard_normal((B, prob.N))
+    c0 = rng.standard_normal((B, prob.N_s))
+    w = rng.standard_normal((B, prob.N))
+    G = lift_matrix(prob)
+    absG = abs(G)
+    rhs = S.lifted_rhs(torch.from_numpy(F).cuda(), torch.from_numpy(c0).cuda()).cpu().numpy()
+    u = S.lift_add(torch.from_numpy(w).cuda(), torch.from_numpy(c0).cuda()).cpu().numpy()
+    for b in range(B):
+        ref = F[b] - G @ c0[b]
+        bound = 1e-13 * (np.abs(F[b]) + absG @ np.abs(c0[b]))
+        assert np.all(np.abs(rhs[b] - ref) <= bound)
+        assert np.array_equal(u[b], w[b] + np.kron(np.ones(prob.n_t), c0[b]))
+    # the output may not overlap an input
+    from paper_1809_10026_gb300 import _lib
+    Fg, cg = torch.from_numpy(F).cuda(), torch.from_numpy(c0).cuda()
+    assert S.lib.stls_lifted_rhs(S.ctx, S._ptr(Fg), S._ptr(cg), S._ptr(Fg)) == _lib.STLS_EINVAL
+    assert S.lib.stls_lift_add(S.ctx, S._ptr(Fg), S._ptr(cg), S._ptr(Fg)) == _lib.STLS_EINVAL
