@@ -274,9 +274,8 @@ def run_form(stls, name, W, F, args, world, sampler=None):
                 clocks=clocks, precision=precision, refine=refine, setup_ms=setup_ms)
 
 
-def cpu_baseline_sample(F, iters):
-    """Oracle FP64 PCG on the same workload, on the host cores: setup + 1 iteration,
-    extrapolated to `iters` iterations."""
+def oracle_iteration_times(F):
+    """(setup s, one PCG iteration s, N) of the oracle's FP64 PCG on the workload."""
     from oracle.system import STProblem
     from oracle.fd import FD
     import numpy as np
@@ -294,13 +293,43 @@ def cpu_baseline_sample(F, iters):
     r -= alpha * q
     _ = np.linalg.norm(r)
     t_iter = time.perf_counter() - t1
+    del x
+    return t_setup, t_iter, prob.N
+
+
+def single_thread_sample(iters, timeout_s=240):
+    """The same sample with one host thread (BLAS and OpenMP pools of 1), in a
+    child process, for comparison with the paper's serial times."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               NUMEXPR_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
+    try:
+        res = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-iteration-sample"],
+                             env=env, capture_output=True, text=True, timeout=timeout_s)
+    except subprocess.TimeoutExpired:
+        return {"skipped": "longer than %d s" % timeout_s}
+    if res.returncode != 0:
+        tail = res.stderr.strip().splitlines()
+        return {"skipped": "child failed: " + (tail[-1] if tail else "exit %d" % res.returncode)}
+    t_setup, t_iter, n = json.loads(res.stdout.strip().splitlines()[-1])
+    solve_s = t_setup + iters * t_iter
+    return {"value": n / solve_s, "unit": "DoF/s", "cores": 1, "solve_s_extrapolated": solve_s,
+            "sample": "oracle setup (%.1f s) + one PCG iteration (%.1f s), one thread, extrapolated to "
+                      "%d iterations" % (t_setup, t_iter, iters)}
+
+
+def cpu_baseline_sample(F, iters, single_thread=True):
+    """Oracle FP64 PCG on the same workload, on the host cores: setup + 1 iteration,
+    extrapolated to `iters` iterations (and the same with one thread)."""
+    t_setup, t_iter, n = oracle_iteration_times(F)
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     solve_s = t_setup + iters * t_iter
-    del x
-    return {"value": prob.N / solve_s, "unit": "DoF/s", "cores": cores, "kind": "oracle",
-            "sample": "oracle setup (%.1f s) + one PCG iteration (%.1f s) on the full workload, "
-                      "extrapolated to %d iterations" % (t_setup, t_iter, iters),
-            "solve_s_extrapolated": solve_s}
+    out = {"value": n / solve_s, "unit": "DoF/s", "cores": cores, "kind": "oracle",
+           "sample": "oracle setup (%.1f s) + one PCG iteration (%.1f s) on the full workload, "
+                     "extrapolated to %d iterations" % (t_setup, t_iter, iters),
+           "solve_s_extrapolated": solve_s}
+    if single_thread:
+        out["single_thread"] = single_thread_sample(iters)
+    return out
 
 
 def run_ours(args):
@@ -487,7 +516,12 @@ def main():
                     help="other forms timed in the same run (comma separated; empty for none)")
     ap.add_argument("--form-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-iteration-sample", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.oracle_iteration_sample:  # child of single_thread_sample
+        from paper_1809_10026_gb300 import synth
+        print(json.dumps(list(oracle_iteration_times(synth.uniform(18125250, WORKLOAD["tag"])))))
+        return
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
