@@ -235,3 +235,28 @@ def test_cube3d_p3_n64_operators_sampled():
     fd = FD(prob)
     zr = fd.apply(x)
     np.testing.assert_allclose(z, zr, rtol=0, atol=fd_tolerance(fd) * np.abs(zr).max())
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(precision="tf32", refine=True)], ids=["fp64", "tf32_refine"])
+def test_solve_host_matches_device_solve(kw):
+    """stls_solve_host (host F and u, copies inside the call; the bench's
+    end-to-end path) gives bit for bit the device solve's u and iteration
+    counts (same kernels, fixed-order reductions), with pageable numpy arrays
+    and with pinned buffers, and the direct solve's u to the tolerance."""
+    B = 2
+    prob = STProblem(2, 3, 6)
+    S = _solver(2, 3, 6, batch=B, **kw)
+    F = synth.uniform(prob.N, 21, batch=B)
+    u_dev, info_d = S.solve(_cuda(F), tol=1e-12, maxit=300)
+    u_dev = u_dev.cpu().numpy()
+    u_host, info_h = S.solve_host(F, tol=1e-12, maxit=300)
+    assert np.array_equal(u_host.reshape(B, prob.N), u_dev)
+    assert [i["iters"] for i in info_h] == [i["iters"] for i in info_d]
+    Fh = torch.from_numpy(F).pin_memory()
+    uh = torch.empty_like(Fh).pin_memory()
+    info_p = S.solve_host_ptr(Fh.data_ptr(), uh.data_ptr(), tol=1e-12, maxit=300)
+    assert np.array_equal(uh.numpy(), u_dev) and info_p[0]["status"] == "ok"
+    A = prob.assemble_A_kron()
+    for b in range(B):
+        ref = direct_solve(A, F[b])
+        assert np.linalg.norm(u_host.reshape(B, -1)[b] - ref) <= 1e-8 * np.linalg.norm(ref)
