@@ -260,3 +260,23 @@ def test_solve_host_matches_device_solve(kw):
     for b in range(B):
         ref = direct_solve(A, F[b])
         assert np.linalg.norm(u_host.reshape(B, -1)[b] - ref) <= 1e-8 * np.linalg.norm(ref)
+
+
+def test_context_factors_and_launch_count():
+    """stls_get_factor returns the context's copies of the host setup's 1D
+    factors (bitwise those of stls_host_factor), and the launch counter
+    advances by the kernels one fused A x launches (slice, z and t passes)."""
+    import paper_1809_10026_gb300 as stls
+    S = _solver(3, 2, [4, 5, 3], 0.8)
+    for which in ("mass", "stiff", "bilap", "eigvec", "eigval"):
+        for k in range(3):
+            ref = stls.host_factor(which, k, 3, 2, [4, 5, 3], T=0.8)
+            assert np.array_equal(S.factor(which, k), ref)
+    for which in ("mass", "stiff", "eigvec", "eigval", "end", "integral"):
+        ref = stls.host_factor(which, 3, 3, 2, [4, 5, 3], T=0.8)
+        assert np.array_equal(S.factor(which, 3), ref)
+    x = _cuda(synth.uniform(S.N, 5))
+    n0 = S.launch_count()
+    S.apply_A(x)
+    torch.cuda.synchronize()
+    assert S.launch_count() - n0 == 3
