@@ -205,7 +205,8 @@ enum stls_factor {
 int stls_get_factor(const stls_ctx *ctx, int which, int dir, double *host_out);
 
 /* Same as stls_get_factor but computed on the host from `prm` alone, without
- * a GPU or a context.  Returns STLS_EINVAL for invalid parameters. */
+ * a GPU or a context.  Returns STLS_EINVAL for invalid parameters, with the
+ * reason in stls_last_error(NULL). */
 int stls_host_factor(const stls_params *prm, int which, int dir, double *host_out);
 
 /* Number of kernels this context has launched since creation. */

@@ -356,10 +356,23 @@ int copy_factor_public(const HostSetup &hs, int which, int dir, double *out) {
 }
 }  // namespace stls
 
+namespace stls {
+void set_thread_error(const std::string &msg);
+}
+
 extern "C" int stls_host_factor(const stls_params *prm, int which, int dir, double *host_out) {
-  if (prm == nullptr) return STLS_EINVAL;
+  stls::set_thread_error("");
+  if (prm == nullptr) {
+    stls::set_thread_error("stls_host_factor: prm is NULL");
+    return STLS_EINVAL;
+  }
   stls::HostSetup hs;
   std::string err;
-  if (!stls::build_setup(*prm, hs, err)) return STLS_EINVAL;
-  return copy_factor(hs, which, dir, host_out);
+  if (!stls::build_setup(*prm, hs, err)) {
+    stls::set_thread_error("stls_host_factor: " + err);
+    return STLS_EINVAL;
+  }
+  const int rc = copy_factor(hs, which, dir, host_out);
+  if (rc != STLS_OK) stls::set_thread_error("stls_host_factor: unknown factor id or direction for it");
+  return rc;
 }

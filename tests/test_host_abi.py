@@ -33,14 +33,29 @@ def test_exports_every_declared_symbol(lib):
 
 
 @pytest.mark.parametrize("bad", [dict(d=4), dict(p_s=1), dict(T=0.0), dict(T=float("nan")),
-                                 dict(n_el_t=0), dict(batch=0), dict(precision=7), dict(fp64_residuals=2)])
+                                 dict(n_el_t=0), dict(batch=0), dict(precision=7), dict(fp64_residuals=2),
+                                 dict(n_el_t=127, p_t=3), dict(n_el_s=(128, 4, 0))])
 def test_invalid_parameters_rejected_on_host(lib, bad):
     prm = _lib.make_params(2, 3, 4)
     for k, v in bad.items():
-        setattr(prm, k, v)
+        if k == "n_el_s":
+            for i, e in enumerate(v):
+                prm.n_el_s[i] = e
+        else:
+            setattr(prm, k, v)
     out = np.zeros(100000)
     rc = lib.stls_host_factor(ctypes.byref(prm), 0, 0, out.ctypes.data_as(ctypes.c_void_p))
     assert rc == _lib.STLS_EINVAL
+    assert lib.stls_last_error(None).startswith(b"stls_host_factor: ")
+
+
+def test_largest_sizes_accepted(lib):
+    """128 basis functions per direction (the dense 1D factors' limit): n_el + p - 2
+    = 128 in space, n_el_t + p_t - 1 = 128 in time."""
+    U = stls.host_factor("eigvec", 0, 2, 3, [127, 4], n_el_t=126)
+    assert U.shape == (128, 128)
+    Ut = stls.host_factor("eigvec", 2, 2, 3, [127, 4], n_el_t=126)
+    assert Ut.shape == (128, 128)
 
 
 def test_create_rejects_invalid_params_before_any_launch(lib):
