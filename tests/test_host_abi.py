@@ -49,6 +49,22 @@ def test_invalid_parameters_rejected_on_host(lib, bad):
     assert lib.stls_last_error(None).startswith(b"stls_host_factor: ")
 
 
+def test_no_gpu_fails_loudly(lib):
+    """Without a usable GPU the product path has no fallback: the binding's
+    Solver raises, and stls_create returns an error with the CUDA reason and
+    no context."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(RuntimeError, match="CUDA"):
+        stls.Solver(2, 3, 4)
+    prm = _lib.make_params(2, 3, 4)
+    ctx = ctypes.c_void_p()
+    rc = lib.stls_create(ctypes.byref(ctx), ctypes.byref(prm), None)
+    assert rc in (_lib.STLS_ENOMEM, _lib.STLS_ECUDA) and ctx.value is None
+    assert lib.stls_last_error(None)
+
+
 def test_largest_sizes_accepted(lib):
     """128 basis functions per direction (the dense 1D factors' limit): n_el + p - 2
     = 128 in space, n_el_t + p_t - 1 = 128 in time."""
