@@ -112,7 +112,9 @@ int stls_create(stls_ctx **out, const stls_params *prm, void *cuda_stream);
 void stls_destroy(stls_ctx *ctx);
 
 /* Text of the last error on this context ("" if none).  With ctx == NULL,
- * the last stls_create failure of the calling thread. */
+ * the last failure of a context-free call on the calling thread
+ * (stls_create, stls_host_factor, stls_round_bf16,
+ * stls_apply_precond_noalloc). */
 const char *stls_last_error(const stls_ctx *ctx);
 
 /* Change the stream used by later calls. */
