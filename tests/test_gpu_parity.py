@@ -189,10 +189,13 @@ def _table1():
     return rows
 
 
-@pytest.mark.parametrize("n_sub", [8, 16, 32])
+@pytest.mark.parametrize("n_sub", [8, 16, 32, 64])
 @pytest.mark.parametrize("p", [2, 3, 4, 5])
 def test_table1_iterations_on_gpu(n_sub, p):
-    """Table 1: P + CG on the cube, tol 1e-8, x0 = 0, u = sin sin sin sin(t)."""
+    """Table 1: P + CG on the cube, tol 1e-8, x0 = 0, u = sin sin sin sin(t).
+    n_sub = 64 is the bench's mesh (17.0 M to 20.5 M unknowns); the oracle's
+    PCG also takes 13 iterations there, with the residual of iteration 12
+    at 1.30e-8 to 1.48e-8, so the count does not hinge on rounding."""
     prob = STProblem(3, p, n_sub)
     F = prob.load_separable(_cube_terms())
     S = _solver(3, p, n_sub)
