@@ -3,6 +3,7 @@
 // preconditioner (Algorithm 1), the PCG / flexible-CG driver and the lifting
 // of a non-zero initial datum (Sec. 3.1).
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -178,7 +179,19 @@ std::vector<double> transpose(const std::vector<double> &A, int n) {
 }
 
 // ---- timing ---------------------------------------------------------------------------
+// Every phase is also an NVTX range of the same name (a no-op unless a
+// profiler is attached); the whole create and solve calls are ranges too.
+const char *const kPhaseName[5] = {"apply_A", "precond", "cg_vectors", "apply_A_f32", "apply_A_df"};
+
+struct NvtxScope {
+  explicit NvtxScope(const char *name) { nvtxRangePushA(name); }
+  ~NvtxScope() { nvtxRangePop(); }
+  NvtxScope(const NvtxScope &) = delete;
+  NvtxScope &operator=(const NvtxScope &) = delete;
+};
+
 int phase_begin(stls_ctx *c, int phase) {
+  nvtxRangePushA(kPhaseName[phase]);
   if (!c->timing) return -1;
   size_t idx = c->ev_pairs.size() * 2;
   while (c->ev_pool.size() < idx + 2) {
@@ -192,6 +205,7 @@ int phase_begin(stls_ctx *c, int phase) {
 }
 
 void phase_end(stls_ctx *c, int idx) {
+  nvtxRangePop();
   if (idx < 0) return;
   cudaEventRecord(c->ev_pool[idx + 1], c->stream);
 }
@@ -761,6 +775,7 @@ void stls_destroy(stls_ctx *ctx) {
 }
 
 int stls_create(stls_ctx **out, const stls_params *prm, void *cuda_stream) {
+  NvtxScope range("stls_create");
   g_create_error.clear();
   if (out == nullptr || prm == nullptr) {
     g_create_error = "out and prm must not be NULL";
@@ -953,6 +968,7 @@ int stls_apply_precond(stls_ctx *c, const double *r, double *z) {
 }
 
 int stls_solve(stls_ctx *c, const double *F, double *u, double tol, int maxit, stls_solve_info *info) {
+  NvtxScope range("stls_solve");
   if (c == nullptr) return STLS_EINVAL;
   if (F == u) return set_err(c, STLS_EINVAL, "solve: F and u must not overlap");
   return c->hs.prm.refine ? solve_ir_impl(c, F, u, tol, maxit, info) : solve_impl(c, F, u, tol, maxit, info);
@@ -960,6 +976,7 @@ int stls_solve(stls_ctx *c, const double *F, double *u, double tol, int maxit, s
 
 int stls_solve_host(stls_ctx *c, const double *F_host, double *u_host, double tol, int maxit,
                     stls_solve_info *info) {
+  NvtxScope range("stls_solve_host");
   if (c == nullptr || F_host == nullptr || u_host == nullptr) return set_err(c, STLS_EINVAL, "NULL argument");
   const size_t bytes = sizeof(double) * static_cast<size_t>(c->B) * c->N;
   STLS_CK(cudaMemcpyAsync(c->dF, F_host, bytes, cudaMemcpyHostToDevice, c->stream), "H2D copy of F");
