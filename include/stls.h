@@ -206,6 +206,16 @@ enum stls_factor {
  * memory.  Matrices are row-major. */
 int stls_get_factor(const stls_ctx *ctx, int which, int dir, double *host_out);
 
+/* Testing hook of the breakdown checks: replaces the eigenvalues of
+ * direction `dir` (0..d-1 space, d time; n values in host memory) that the
+ * FP64 preconditioner divides by (Algorithm 1, step 3), after the work queued
+ * on the context's stream has finished.  With values that make some
+ * lambda_t[i_t] + sum_k lambda_k[i_k] negative, P is indefinite and a solve
+ * stops with STLS_EBREAKDOWN.  stls_get_factor(STLS_F_EIGVAL) returns the new
+ * values; the eigenvectors are unchanged.  Errors: STLS_EINVAL for a mixed
+ * precision context, dir out of range or NULL values. */
+int stls_override_eigenvalues(stls_ctx *ctx, int dir, const double *lam_host);
+
 /* Same as stls_get_factor but computed on the host from `prm` alone, without
  * a GPU or a context.  Returns STLS_EINVAL for invalid parameters, with the
  * reason in stls_last_error(NULL). */

@@ -209,6 +209,16 @@ class Solver:
                                         out.ctypes.data_as(ctypes.c_void_p)), self.ctx)
         return out if size == n else out.reshape(n, n)
 
+    def override_eigenvalues(self, direction, lam):
+        """Testing hook: the FP64 preconditioner divides by these eigenvalues of
+        `direction` from now on (stls_override_eigenvalues)."""
+        n = self.n_s[direction] if direction < self.d else self.n_t
+        lam = np.ascontiguousarray(lam, dtype=np.float64)
+        if lam.size != n:
+            raise ValueError("expected %d eigenvalues" % n)
+        _check(self.lib.stls_override_eigenvalues(self.ctx, int(direction), lam.ctypes.data_as(ctypes.c_void_p)),
+               self.ctx)
+
     def launch_count(self):
         return int(self.lib.stls_launch_count(self.ctx))
 

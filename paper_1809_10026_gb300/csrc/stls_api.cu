@@ -457,6 +457,21 @@ int fd_apply_impl(stls_ctx *c, const double *r, double *z) {
   return STLS_OK;
 }
 
+// lambda_s[c] = sum_k lambda_k[i_k(c)] over the colexicographic spatial index
+std::vector<double> spatial_eigenvalue_sums(const stls_ctx *c) {
+  std::vector<double> ls(c->Ns, 0.0);
+  for (long long idx = 0; idx < c->Ns; ++idx) {
+    long long rem = idx;
+    double s = 0.0;
+    for (int k = 0; k < c->d; ++k) {
+      s += c->hs.eig_s[k].lam[rem % c->n_s[k]];
+      rem /= c->n_s[k];
+    }
+    ls[idx] = s;
+  }
+  return ls;
+}
+
 int check_ptr(stls_ctx *c, const void *ptr, const char *name) {
   if (ptr == nullptr || (reinterpret_cast<uintptr_t>(ptr) & 7u) != 0)
     return set_err(c, STLS_EINVAL, std::string(name) + " is NULL or not 8-byte aligned");
@@ -845,20 +860,7 @@ int stls_create(stls_ctx **out, const stls_params *prm, void *cuda_stream) {
   if (!rc) rc = upload(c, &c->m_int, Tm.integrals);
   if (!rc) rc = upload(c, &c->ones_t, std::vector<double>(Tm.n, 1.0));
   if (!rc) rc = upload(c, &c->zeros_t, std::vector<double>(Tm.n, 0.0));
-  if (!rc) {
-    // lambda_s[c] = sum_k lambda_k[i_k(c)] over the colexicographic spatial index
-    std::vector<double> ls(c->Ns, 0.0);
-    for (long long idx = 0; idx < c->Ns; ++idx) {
-      long long rem = idx;
-      double s = 0.0;
-      for (int k = 0; k < c->d; ++k) {
-        s += c->hs.eig_s[k].lam[rem % c->n_s[k]];
-        rem /= c->n_s[k];
-      }
-      ls[idx] = s;
-    }
-    rc = upload(c, &c->lam_s, ls);
-  }
+  if (!rc) rc = upload(c, &c->lam_s, spatial_eigenvalue_sums(c));
   if (rc) return fail(rc);
   const size_t BN = static_cast<size_t>(c->B) * c->N, BNs = static_cast<size_t>(c->B) * c->Ns;
   double **vecs[] = {&c->r, &c->p, &c->q, &c->z, &c->fd_tmp[0], &c->fd_tmp[1], &c->dF, &c->du};
@@ -1052,6 +1054,27 @@ int stls_lift_adjoint(stls_ctx *c, const double *g, const double *lam, double *d
   const long long n = static_cast<long long>(c->B) * c->Ns;
   STLS_LAUNCH(stls::launch_axpy(gs, La, -1.0, dc0, n, c->stream), "axpy");
   STLS_LAUNCH(stls::launch_axpy(dc0, Jb, -1.0, dc0, n, c->stream), "axpy");
+  return STLS_OK;
+}
+
+int stls_override_eigenvalues(stls_ctx *c, int dir, const double *lam_host) {
+  if (c == nullptr) return STLS_EINVAL;
+  if (c->hs.prm.precision != STLS_FP64)
+    return set_err(c, STLS_EINVAL, "override_eigenvalues: FP64 contexts only");
+  if (dir < 0 || dir > c->d || lam_host == nullptr)
+    return set_err(c, STLS_EINVAL, "override_eigenvalues: dir out of range or NULL values");
+  // work already queued may still read the eigenvalues
+  STLS_CK(cudaStreamSynchronize(c->stream), "sync");
+  if (dir == c->d) {
+    std::vector<double> &lam = c->hs.eig_t.lam;
+    std::copy(lam_host, lam_host + lam.size(), lam.begin());
+    STLS_CK(cudaMemcpy(c->lam_t, lam.data(), lam.size() * sizeof(double), cudaMemcpyHostToDevice), "upload");
+  } else {
+    std::vector<double> &lam = c->hs.eig_s[dir].lam;
+    std::copy(lam_host, lam_host + lam.size(), lam.begin());
+    const std::vector<double> ls = spatial_eigenvalue_sums(c);
+    STLS_CK(cudaMemcpy(c->lam_s, ls.data(), ls.size() * sizeof(double), cudaMemcpyHostToDevice), "upload");
+  }
   return STLS_OK;
 }
 

@@ -283,3 +283,35 @@ def test_context_factors_and_launch_count():
     S.apply_A(x)
     torch.cuda.synchronize()
     assert S.launch_count() - n0 == 3
+
+
+def test_indefinite_preconditioner_reports_breakdown():
+    """Failure detection on the host side: eigenvalues overridden so that one
+    entry of the eigenvalue tensor is slightly negative make P indefinite;
+    (z, r) < 0 then (the oracle's FD with the same values gives (z, r) < 0 for
+    every seed tried), and the solve stops with a breakdown status instead of
+    iterating on.  The context stays usable."""
+    import paper_1809_10026_gb300 as stls
+    prob = STProblem(2, 3, 4)
+    S = _solver(2, 3, 4)
+    F = synth.uniform(prob.N, 0)
+    u, info = S.solve(_cuda(F), tol=1e-10)
+    assert info[0]["status"] == "ok"
+    l1, l2, lt = S.factor("eigval", 0), S.factor("eigval", 1), S.factor("eigval", 2)
+    s = l1[0] + l2[0]
+    bad = lt.copy()
+    bad[0] = -s - 1e-9 * (s + abs(lt[0]))
+    fd = FD(prob)
+    fd.lam_t = bad.copy()
+    assert F @ fd.apply(F) < 0
+    S.override_eigenvalues(2, bad)
+    assert np.array_equal(S.factor("eigval", 2), bad)
+    u, info = S.solve(_cuda(F), tol=1e-10, check=False)
+    assert info[0]["status"] == "breakdown"
+    with pytest.raises(RuntimeError, match="breakdown"):
+        S.solve(_cuda(F), tol=1e-10)
+    S.override_eigenvalues(2, lt)  # restored: the context solves again
+    u, info = S.solve(_cuda(F), tol=1e-10)
+    assert info[0]["status"] == "ok"
+    with pytest.raises(RuntimeError):
+        stls.Solver(2, 3, 4, precision="bf16").override_eigenvalues(2, lt)
