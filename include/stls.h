@@ -206,6 +206,16 @@ enum stls_factor {
  * memory.  Matrices are row-major. */
 int stls_get_factor(const stls_ctx *ctx, int which, int dir, double *host_out);
 
+/* Relative residuals ||r_k|| / ||F|| of right-hand side b (0..B-1) in the
+ * last solve on this context, as the convergence test saw them: entry 0 is
+ * the initial residual (1, or 0 when F = 0), then one entry per CG iteration
+ * (refine = 0: the recursively updated residual) or per outer step
+ * (refine = 1: the outer residual F - A u; where a provisional double-float
+ * residual was recomputed in FP64, the FP64 value).  Writes min(*len,
+ * max_len) values to host_out (may be NULL to ask for the length) and the
+ * length to *len; 0 before the first solve.  Errors: STLS_EINVAL. */
+int stls_residual_history(const stls_ctx *ctx, int b, double *host_out, int max_len, int *len);
+
 /* Testing hook of the breakdown checks: replaces the eigenvalues of
  * direction `dir` (0..d-1 space, d time; n values in host memory) that the
  * FP64 preconditioner divides by (Algorithm 1, step 3), after the work queued

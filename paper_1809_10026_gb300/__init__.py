@@ -209,6 +209,15 @@ class Solver:
                                         out.ctypes.data_as(ctypes.c_void_p)), self.ctx)
         return out if size == n else out.reshape(n, n)
 
+    def residual_history(self, b=0):
+        """||r_k|| / ||F|| of right-hand side b in the last solve (stls_residual_history)."""
+        n = ctypes.c_int()
+        _check(self.lib.stls_residual_history(self.ctx, int(b), None, 0, ctypes.byref(n)), self.ctx)
+        out = np.zeros(n.value)
+        _check(self.lib.stls_residual_history(self.ctx, int(b), out.ctypes.data_as(ctypes.c_void_p), n.value,
+                                              ctypes.byref(n)), self.ctx)
+        return out
+
     def override_eigenvalues(self, direction, lam):
         """Testing hook: the FP64 preconditioner divides by these eigenvalues of
         `direction` from now on (stls_override_eigenvalues)."""

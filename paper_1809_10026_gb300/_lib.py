@@ -13,7 +13,7 @@ FACTOR = {"mass": 0, "stiff": 1, "bilap": 2, "eigvec": 3, "eigval": 4, "end": 5,
 
 EXPORTS = ["stls_create", "stls_destroy", "stls_last_error", "stls_set_stream", "stls_sizes",
            "stls_apply_A", "stls_apply_A_df", "stls_apply_precond", "stls_solve", "stls_solve_host", "stls_apply_lift",
-           "stls_lifted_rhs", "stls_lift_add", "stls_lift_adjoint", "stls_override_eigenvalues", "stls_get_factor", "stls_host_factor", "stls_launch_count",
+           "stls_lifted_rhs", "stls_lift_add", "stls_lift_adjoint", "stls_override_eigenvalues", "stls_residual_history", "stls_get_factor", "stls_host_factor", "stls_launch_count",
            "stls_enable_timing", "stls_phase_times", "stls_phase_times_n", "stls_apply_precond_noalloc", "stls_round_bf16"]
 
 
@@ -68,6 +68,7 @@ def load():
     lib.stls_lift_add.argtypes = [vp, vp, vp, vp]
     lib.stls_lift_adjoint.argtypes = [vp, vp, vp, vp]
     lib.stls_override_eigenvalues.argtypes = [vp, i, vp]
+    lib.stls_residual_history.argtypes = [vp, i, vp, i, ctypes.POINTER(ctypes.c_int)]
     lib.stls_get_factor.argtypes = [vp, i, i, vp]
     lib.stls_host_factor.argtypes = [ctypes.POINTER(Params), i, i, vp]
     lib.stls_launch_count.argtypes = [vp]

@@ -66,6 +66,7 @@ struct stls_ctx {
   stls::RedWork rw{};
   stls::TcFd tc{};
   std::vector<void *> allocations;
+  std::vector<std::vector<double>> hist;  // relative residuals of the last solve, per RHS
   long long launches = 0;
   std::string err;
   // timing
@@ -472,6 +473,22 @@ std::vector<double> spatial_eigenvalue_sums(const stls_ctx *c) {
   return ls;
 }
 
+// Residual history: after every read of the solver state, entry `iters` of
+// right-hand side b holds its latest relative residual (a new entry per
+// iteration or outer step; a recomputed residual overwrites its entry).
+constexpr int kMaxHistory = 1 << 20;
+void history_reset(stls_ctx *c) { c->hist.assign(c->B, std::vector<double>(1, 1.0)); }
+void history_record(stls_ctx *c) {
+  for (int b = 0; b < c->B && b < static_cast<int>(c->hist.size()); ++b) {
+    const CGState &s = c->st_host[b];
+    if (s.iters < 0 || s.iters >= kMaxHistory) continue;
+    std::vector<double> &h = c->hist[b];
+    if (static_cast<int>(h.size()) < s.iters + 1) h.resize(s.iters + 1, s.rel_res);
+    h[s.iters] = s.rel_res;
+    if (!(s.nF2 > 0.0)) h[0] = 0.0;  // F = 0: u = 0 with a zero residual
+  }
+}
+
 int check_ptr(stls_ctx *c, const void *ptr, const char *name) {
   if (ptr == nullptr || (reinterpret_cast<uintptr_t>(ptr) & 7u) != 0)
     return set_err(c, STLS_EINVAL, std::string(name) + " is NULL or not 8-byte aligned");
@@ -484,6 +501,7 @@ int solve_impl(stls_ctx *c, const double *F, double *u, double tol, int maxit, s
   const long long N = c->N;
   const int B = c->B;
   const int flex = c->hs.prm.flexible;
+  history_reset(c);
   int ph = phase_begin(c, 2);
   STLS_LAUNCH(stls::launch_cg_init(F, u, c->r, N, B, c->st, c->rw, c->stream), "cg_init");
   phase_end(c, ph);
@@ -507,6 +525,7 @@ int solve_impl(stls_ctx *c, const double *F, double *u, double tol, int maxit, s
     STLS_CK(cudaMemcpyAsync(c->st_host, c->st, sizeof(CGState) * B, cudaMemcpyDeviceToHost, c->stream),
             "state copy");
     STLS_CK(cudaStreamSynchronize(c->stream), "sync");
+    history_record(c);
     if (c->hs.prm.precision != STLS_FP64 && stls::tc_fd_error(c->tc))
       return set_err(c, STLS_ECUDA, "tensor-core FD apply: a bounded mbarrier wait timed out");
     bool any = false;
@@ -528,6 +547,7 @@ int solve_impl(stls_ctx *c, const double *F, double *u, double tol, int maxit, s
   STLS_CK(cudaMemcpyAsync(c->st_host, c->st, sizeof(CGState) * B, cudaMemcpyDeviceToHost, c->stream),
           "state copy");
   STLS_CK(cudaStreamSynchronize(c->stream), "sync");
+  history_record(c);
   if (c->timing) collect_phases(c);
   int first_bad = STLS_OK;
   for (int b = 0; b < B; ++b) {
@@ -575,6 +595,7 @@ int solve_ir_impl(stls_ctx *c, const double *F, double *u, double tol, int maxit
   const double eta_fixed = c->hs.prm.inner_tol, eta_min = 1e-4, kStep = 1e-3;
   const int kMaxOuter = 100, kMaxInnerPerOuter = 400;
   double *r64 = c->r, *q64 = c->q;
+  history_reset(c);
   int ph = phase_begin(c, 2);
   STLS_LAUNCH(stls::launch_cg_init(F, u, r64, N, B, c->st, c->rw, c->stream), "cg_init");
   phase_end(c, ph);
@@ -599,6 +620,7 @@ int solve_ir_impl(stls_ctx *c, const double *F, double *u, double tol, int maxit
     STLS_CK(cudaMemcpyAsync(c->st_host, c->st, sizeof(CGState) * B, cudaMemcpyDeviceToHost, c->stream),
             "state copy");
     STLS_CK(cudaStreamSynchronize(c->stream), "sync");
+    history_record(c);
     return STLS_OK;
   };
   std::vector<CGState> inner_host(B);
@@ -741,6 +763,7 @@ int solve_ir_impl(stls_ctx *c, const double *F, double *u, double tol, int maxit
   STLS_CK(cudaMemcpyAsync(c->st_host, c->st, sizeof(CGState) * B, cudaMemcpyDeviceToHost, c->stream),
           "state copy");
   STLS_CK(cudaStreamSynchronize(c->stream), "sync");
+  history_record(c);
   if (c->timing) collect_phases(c);
   int first_bad = STLS_OK;
   for (int b = 0; b < B; ++b) {
@@ -1075,6 +1098,15 @@ int stls_override_eigenvalues(stls_ctx *c, int dir, const double *lam_host) {
     const std::vector<double> ls = spatial_eigenvalue_sums(c);
     STLS_CK(cudaMemcpy(c->lam_s, ls.data(), ls.size() * sizeof(double), cudaMemcpyHostToDevice), "upload");
   }
+  return STLS_OK;
+}
+
+int stls_residual_history(const stls_ctx *c, int b, double *host_out, int max_len, int *len) {
+  if (c == nullptr || b < 0 || b >= c->B || len == nullptr || max_len < 0) return STLS_EINVAL;
+  static const std::vector<double> kNone;
+  const std::vector<double> &h = b < static_cast<int>(c->hist.size()) ? c->hist[b] : kNone;
+  *len = static_cast<int>(h.size());
+  if (host_out != nullptr) std::copy(h.begin(), h.begin() + std::min<size_t>(h.size(), max_len), host_out);
   return STLS_OK;
 }
 

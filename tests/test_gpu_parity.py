@@ -315,3 +315,37 @@ def test_indefinite_preconditioner_reports_breakdown():
     assert info[0]["status"] == "ok"
     with pytest.raises(RuntimeError):
         stls.Solver(2, 3, 4, precision="bf16").override_eigenvalues(2, lt)
+
+
+@pytest.mark.parametrize("d,p,n_el", [(1, 3, 12), (2, 2, 7), (3, 3, 4)])
+def test_residual_history_matches_oracle_pcg(d, p, n_el):
+    """The PCG residual recurrence step by step: the relative residual of every
+    iteration (stls_residual_history) equals the oracle PCG's (same algorithm,
+    FP64, same stopping rule; rounding differs by far less than 1e-9
+    relative over a dozen iterations of a well-conditioned system)."""
+    prob = STProblem(d, p, n_el)
+    F = synth.uniform(prob.N, 50 + d)
+    S = _solver(d, p, n_el)
+    assert len(S.residual_history()) == 0  # before any solve
+    u, info = S.solve(_cuda(F), tol=1e-11, maxit=200)
+    h = S.residual_history()
+    _, it, h_ref = pcg(prob.apply_A_kron, FD(prob).apply, F, 1e-11, 200)
+    assert info[0]["iters"] == it == len(h) - 1
+    np.testing.assert_allclose(h, h_ref, rtol=1e-9, atol=0)
+    assert h[-1] == info[0]["rel_res"] <= 1e-11
+
+
+def test_residual_history_refinement_and_batch():
+    """Refinement form: one entry per outer step, ending with the FP64 residual
+    the solve reports; a zero right-hand side has the history [0]."""
+    B = 2
+    prob = STProblem(3, 3, 5)
+    F = synth.uniform(prob.N, 61, batch=B)
+    F[1] = 0.0
+    S = _solver(3, 3, 5, precision="tf32", refine=True, batch=B)
+    u, info = S.solve(_cuda(F), tol=1e-10, maxit=400)
+    h0, h1 = S.residual_history(0), S.residual_history(1)
+    assert len(h0) == info[0]["outer"] + 1 and h0[0] == 1.0
+    assert h0[-1] == info[0]["rel_res"]
+    assert h0[-1] <= 1e-10 and np.all(np.diff(h0) < 0)
+    assert list(h1) == [0.0]
