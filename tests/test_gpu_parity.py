@@ -300,7 +300,7 @@ def test_indefinite_preconditioner_reports_breakdown():
     l1, l2, lt = S.factor("eigval", 0), S.factor("eigval", 1), S.factor("eigval", 2)
     s = l1[0] + l2[0]
     bad = lt.copy()
-    bad[0] = -s - 1e-9 * (s + abs(lt[0]))
+    bad[0] = -s - 1e-6 * (s + abs(lt[0]))
     fd = FD(prob)
     fd.lam_t = bad.copy()
     assert F @ fd.apply(F) < 0
