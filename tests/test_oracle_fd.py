@@ -75,7 +75,7 @@ def _table1():
     return rows
 
 
-@pytest.mark.parametrize("n_sub", [8, 16])
+@pytest.mark.parametrize("n_sub", [8, 16, 32])
 @pytest.mark.parametrize("p", [2, 3, 4, 5])
 def test_table1_iteration_counts(n_sub, p):
     """P + CG on the cube, tol 1e-8, x0 = 0, u = sin sin sin sin(t) (Table 1)."""
