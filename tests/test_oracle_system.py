@@ -111,6 +111,36 @@ def test_convergence_rates(p, norm, rate):
     assert abs(observed - rate) < 0.35, (errs, observed)
 
 
+def sin_solution_2d():
+    """u = sin(pi x) sin(pi y) sin(t) (the two-dimensional manufactured solution)."""
+    s = lambda x: np.sin(PI * x)
+    terms = [(1.0, np.cos, [s, s]), (2 * PI ** 2, np.sin, [s, s])]
+    exact = {
+        "u": lambda xs, t: np.sin(PI * xs[0]) * np.sin(PI * xs[1]) * np.sin(t),
+        "ut": lambda xs, t: np.sin(PI * xs[0]) * np.sin(PI * xs[1]) * np.cos(t),
+        "lap": lambda xs, t: -2 * PI ** 2 * np.sin(PI * xs[0]) * np.sin(PI * xs[1]) * np.sin(t),
+        "grad": lambda xs, t: [PI * np.cos(PI * xs[0]) * np.sin(PI * xs[1]) * np.sin(t),
+                               PI * np.sin(PI * xs[0]) * np.cos(PI * xs[1]) * np.sin(t)],
+    }
+    return terms, exact
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_convergence_rates_2d(p):
+    """Two space dimensions: V0 h^(p-1) (Theorem 3), H1 h^p, L2 h^(p+1) for
+    p = 3 and h^2 for p = 2 (Sec. 5.1), on n_el = 4, 8, 16."""
+    terms, exact = sin_solution_2d()
+    errs = []
+    for n in (4, 8, 16):
+        prob = STProblem(2, p, n, 1.0)
+        u = direct_solve(prob.assemble_A_kron(), prob.load_separable(terms))
+        errs.append(errors(prob, u, exact))
+    expected = {"V0": p - 1, "H1": p, "L2": p + 1 if p >= 3 else 2}
+    for norm, rate in expected.items():
+        observed = np.log2(errs[-2][norm] / errs[-1][norm])
+        assert abs(observed - rate) < 0.35, (norm, observed)
+
+
 @pytest.mark.parametrize("p_t", [2, 3])
 def test_unbalanced_degrees_gain_one_order(p_t):
     """Spatial degree p_s = p_t + 1: the V0 error converges as h^(p_t), one
