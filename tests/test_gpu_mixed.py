@@ -207,25 +207,3 @@ def test_contexts_of_different_sizes_coexist(form):
 
 def _cuda_arr(x):
     return torch.from_numpy(np.ascontiguousarray(x)).cuda()
-
-
-@pytest.mark.parametrize("fp64_residuals", [False, True])
-def test_headline_solve_cube3d_p3_n64_tf32_refinement(fp64_residuals):
-    """The bench's solve as the bench runs it: 3D, p = 3, 64 elements
-    (18,125,250 unknowns), F ~ U[-1,1] (seed tag 4), TF32 refinement form,
-    tol 1e-8.  The oracle recomputes the residual ||F - A u|| / ||F|| of the
-    returned u with its own Kronecker-factored A: it is below the tolerance and
-    agrees with the library's FP64 residual to 1e-11 (both FP64; their
-    rounding differs by ~1e-14 relative to ||F|| at the solution)."""
-    prob = STProblem(3, 3, 64)
-    S = _solver(3, 3, 64, precision="tf32", refine=True, fp64_residuals=fp64_residuals)
-    assert S.N == prob.N == 18125250
-    F = synth.uniform(prob.N, 4)
-    u, info = S.solve(torch.from_numpy(F).cuda(), tol=1e-8, maxit=200)
-    it = info[0]
-    assert it["status"] == "ok" and it["true_rel_res"] <= 1e-8
-    assert it["iters"] <= 30 and it["outer"] <= 4
-    assert (it["outer_df"] == 0) if fp64_residuals else (it["outer_df"] >= 1)
-    u = u.cpu().numpy()
-    res = np.linalg.norm(F - prob.apply_A_kron(u)) / np.linalg.norm(F)
-    assert res <= 1e-8 + 1e-11 and abs(res - it["true_rel_res"]) <= 1e-11, (res, it)
