@@ -60,3 +60,35 @@ def test_roofline_entry_keys_and_rate(phase, precision, refine, bound, unit):
 
 def test_roofline_entry_without_calls_is_none():
     assert bench.roofline_entry("precond", 0.0, 0, fake_solver("tf32"), 3, PEAKS, True) is None
+
+
+def test_single_thread_sample_parsing(monkeypatch):
+    """The one-thread oracle sample runs in a child process with one-thread
+    pools; the parent turns its JSON line into the cpu_baseline entry, and a
+    failing or slow child becomes a 'skipped' note instead of an error."""
+    import subprocess
+
+    seen = {}
+
+    def fake_run(cmd, env=None, capture_output=None, text=None, timeout=None):
+        seen["cmd"], seen["env"] = cmd, env
+        return subprocess.CompletedProcess(cmd, 0, stdout="noise\n[0.5, 2.0, 1000]\n", stderr="")
+
+    monkeypatch.setattr(bench.subprocess, "run", fake_run)
+    out = bench.single_thread_sample(17)
+    assert seen["cmd"][-1] == "--oracle-iteration-sample"
+    assert seen["env"]["OMP_NUM_THREADS"] == "1" and seen["env"]["OPENBLAS_NUM_THREADS"] == "1"
+    assert out["cores"] == 1 and out["solve_s_extrapolated"] == pytest.approx(0.5 + 17 * 2.0)
+    assert out["value"] == pytest.approx(1000 / (0.5 + 17 * 2.0))
+
+    def failing(cmd, **kw):
+        return subprocess.CompletedProcess(cmd, 1, stdout="", stderr="Traceback\nMemoryError")
+
+    monkeypatch.setattr(bench.subprocess, "run", failing)
+    assert bench.single_thread_sample(17) == {"skipped": "child failed: MemoryError"}
+
+    def slow(cmd, **kw):
+        raise subprocess.TimeoutExpired(cmd, kw.get("timeout"))
+
+    monkeypatch.setattr(bench.subprocess, "run", slow)
+    assert "skipped" in bench.single_thread_sample(17, timeout_s=1)
