@@ -92,3 +92,16 @@ def test_single_thread_sample_parsing(monkeypatch):
 
     monkeypatch.setattr(bench.subprocess, "run", slow)
     assert "skipped" in bench.single_thread_sample(17, timeout_s=1)
+
+
+def test_oracle_iteration_sample_child():
+    """The child entry point itself: one oracle PCG iteration on the full
+    workload (about 10 s on one core), printed as [setup s, iteration s, N]."""
+    import json
+    import subprocess
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
+    res = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--oracle-iteration-sample"],
+                         env=env, capture_output=True, text=True, timeout=600)
+    assert res.returncode == 0, res.stderr[-2000:]
+    t_setup, t_iter, n = json.loads(res.stdout.strip().splitlines()[-1])
+    assert n == N and t_setup >= 0 and t_iter > 0
