@@ -22,6 +22,13 @@ preconditioner in TF32/BF16) and the FP64 PCG.
                   [--precision tf32|bf16|fp64] [--no-refine] [--fp64-residuals]
                   [--forms a,b,...]
 
+Also in the line: "sweep", the degree sweep of this workload's size (p = 2..6
+with 67 - p elements per direction, N = 18,125,250 for every p) in the
+headline form and the FP64 PCG; and "errors_vs_oracle", the relative error
+||u - u_oracle|| / ||u_oracle|| of every form's solution, u_oracle from the
+oracle's FP64 PCG on the host cores to a residual of 1e-12 (run after the GPU
+timing; the same run gives the CPU baseline's measured time to 1e-8).
+
 With --gpus N > 1 (under torchrun) every rank solves its own copy of the
 workload (replicas; the method has no data-path exchange on one node) and
 value = N_dof * steps * ranks / max-over-ranks time.  --impl reference times
@@ -65,16 +72,23 @@ def load_peaks():
         with open(path) as f:
             pk = json.load(f)
         return {"hbm_gbs": pk["hbm_gbs"], "bf16_tflops": pk["bf16_tflops"],
-                "bf16_tflops_sustained": pk.get("bf16_tflops_sustained"), "source": "measured"}
+                "bf16_tflops_sustained": pk.get("bf16_tflops_sustained"), "source": "measured",
+                "sm_max_mhz": pk.get("sm_max_mhz", 2070.0)}
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
-            "source": "fallback"}
+            "source": "fallback", "sm_max_mhz": 2070.0}
 
 
 # FP64 peak: nominal 1.25 TFLOP/s per GB300 (152 SMs); a DFMA probe on this machine
 # measured 1.19 TFLOP/s.
 FP64_PEAK_TFLOPS = 1.25
-# FP32 CUDA-core peak: 152 SMs x 128 FMA/clk x 2 flop x 2.07 GHz (maximum SM clock)
+# FP32 CUDA-core peak: SMs x 128 FMA/clk x 2 flop x maximum SM clock; this default
+# is GB300's 152 SMs at 2.07 GHz, and run_ours replaces it by the device's SM
+# count and the maximum SM clock of MEASURED_PEAKS.json (fp32_peak_tflops)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def fp32_peak_tflops(sms, sm_mhz):
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
 class ClockSampler:
@@ -235,16 +249,18 @@ def roofline_entry(phase, ms, count, S, p, peaks, refine):
              "kernel": "A x, FP64 fused banded mode products", "peak_source": "nominal FP64 1.25 TFLOP/s"}
     elif phase == "apply_A_f32":
         ach = apply_A_flops(S, p) / per / 1e12
-        e = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+        f32 = peaks.get("fp32_tflops", FP32_PEAK_TFLOPS)
+        e = {"bound": "alu", "achieved": ach, "peak": f32, "unit": "TFLOP/s",
              "kernel": "A x, FP32 fused banded mode products",
-             "peak_source": "FP32 FMA units x max SM clock (152 x 128 x 2 x 2.07 GHz)"}
+             "peak_source": peaks.get("fp32_source", "FP32 FMA units x max SM clock (152 x 128 x 2 x 2.07 GHz)")}
     elif phase == "apply_A_df":
         # 12 FP32 operations per banded term (an FMA counts as one operation)
         ops = 12 * apply_A_flops(S, p) / 2
         ach = ops / per / 1e12
-        e = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS / 2, "unit": "Top/s",
+        f32 = peaks.get("fp32_tflops", FP32_PEAK_TFLOPS)
+        e = {"bound": "alu", "achieved": ach, "peak": f32 / 2, "unit": "Top/s",
              "kernel": "A x, double-float fused banded mode products (with the split of u)",
-             "peak_source": "FP32 operations: 152 SMs x 128 lanes x 2.07 GHz"}
+             "peak_source": "FP32 operations: SMs x 128 lanes x max SM clock"}
     else:
         return None
     e["frac"] = e["achieved"] / e["peak"]
@@ -271,7 +287,25 @@ def run_form(stls, name, W, F, args, world, sampler=None):
     ms_max = max_over_ranks(ms, world, F.device)
     _, _, _, phases = timed_solves(S, F, u, W["tol"], 1, 0, world, True)
     return dict(S=S, u=u, ms=ms_max, infos=infos, launches=launches, phases=phases, steps=steps,
-                clocks=clocks, precision=precision, refine=refine, setup_ms=setup_ms)
+                clocks=clocks, precision=precision, refine=refine, setup_ms=setup_ms,
+                u_host=u.cpu().numpy())
+
+
+def sweep_entry(stls, p, form, F, args, world):
+    """One solve form on the degree-sweep workload of degree p (67 - p elements
+    per direction, the N of the main workload)."""
+    W = dict(WORKLOAD, p=p, n_el=67 - p)
+    r = run_form(stls, form, W, F, args, world)
+    S, ph = r["S"], r["phases"]
+    total = sum(v[0] for v in ph.values())
+    it = r["infos"][-1]
+    out = {"form": form, "n_el": W["n_el"], "value": replica_rate(S.N, r["steps"], world, r["ms"]),
+           "unit": "DoF/s", "ms_per_step": r["ms"] / r["steps"], "steps": r["steps"],
+           "iterations": it["iters"], "outer": it["outer"], "true_rel_res": it["true_rel_res"],
+           "phase_share": {k: v[0] / total for k, v in ph.items() if v[1]} if total else None,
+           "phase_ms_per_solve": {k: v[0] for k, v in ph.items() if v[1]}}
+    S.close()
+    return out
 
 
 def oracle_iteration_times(F):
@@ -297,6 +331,32 @@ def oracle_iteration_times(F):
     return t_setup, t_iter, prob.N
 
 
+def oracle_reference_solve(F, tol_ref=1e-12, tol=1e-8):
+    """The oracle's FP64 PCG (oracle.solve.pcg with the FD preconditioner and
+    the Kronecker-factored A) on the workload to tol_ref, on all host cores.
+    Returns (u, seconds from setup start to the first iterate with residual
+    <= tol, iterations to tol, iterations to tol_ref, setup seconds)."""
+    from oracle.system import STProblem
+    from oracle.fd import FD
+    from oracle.solve import pcg
+    W = WORKLOAD
+    t0 = time.perf_counter()
+    prob = STProblem(W["d"], W["p"], W["n_el"], W["T"])
+    fd = FD(prob)
+    t_setup = time.perf_counter() - t0
+    stamps = []  # entry of every preconditioner call: call k + 1 starts right after iteration k
+
+    def apply_P(r):
+        stamps.append(time.perf_counter())
+        return fd.apply(r)
+
+    u, its, hist = pcg(prob.apply_A_kron, apply_P, F, tol_ref, 400)
+    t_end = time.perf_counter()
+    k_tol = next(k for k, h in enumerate(hist) if h <= tol)
+    t_tol = (stamps[k_tol] if k_tol < len(stamps) else t_end) - t0
+    return u, t_tol, k_tol, its, t_setup
+
+
 def single_thread_sample(iters, timeout_s=240):
     """The same sample with one host thread (BLAS and OpenMP pools of 1), in a
     child process, for comparison with the paper's serial times."""
@@ -317,16 +377,32 @@ def single_thread_sample(iters, timeout_s=240):
                       "%d iterations" % (t_setup, t_iter, iters)}
 
 
+def host_cores():
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+
+
 def cpu_baseline_sample(F, iters, single_thread=True):
     """Oracle FP64 PCG on the same workload, on the host cores: setup + 1 iteration,
     extrapolated to `iters` iterations (and the same with one thread)."""
     t_setup, t_iter, n = oracle_iteration_times(F)
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     solve_s = t_setup + iters * t_iter
-    out = {"value": n / solve_s, "unit": "DoF/s", "cores": cores, "kind": "oracle",
+    out = {"value": n / solve_s, "unit": "DoF/s", "cores": host_cores(), "kind": "oracle",
            "sample": "oracle setup (%.1f s) + one PCG iteration (%.1f s) on the full workload, "
                      "extrapolated to %d iterations" % (t_setup, t_iter, iters),
            "solve_s_extrapolated": solve_s}
+    if single_thread:
+        out["single_thread"] = single_thread_sample(iters)
+    return out
+
+
+def cpu_baseline_from_solve(n, t_tol, k_tol, t_setup, iters, single_thread=True):
+    """The CPU baseline measured by the oracle's own solve of the workload: setup
+    plus the iterations up to the first residual <= 1e-8."""
+    out = {"value": n / t_tol, "unit": "DoF/s", "cores": host_cores(), "kind": "oracle",
+           "sample": "the oracle's FP64 PCG solve of the full workload, timed from setup (%.1f s) to the "
+                     "iterate with residual <= 1e-8 (%d iterations, %.1f s); the same run continued to "
+                     "1e-12 for the error check" % (t_setup, k_tol, t_tol),
+           "solve_s": t_tol}
     if single_thread:
         out["single_thread"] = single_thread_sample(iters)
     return out
@@ -341,6 +417,9 @@ def run_ours(args):
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
     peaks = load_peaks()
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    peaks["fp32_tflops"] = fp32_peak_tflops(sms, peaks["sm_max_mhz"])
+    peaks["fp32_source"] = "FP32 FMA units x max SM clock (%d SMs x 128 x 2 x %.0f MHz)" % (sms, peaks["sm_max_mhz"])
     W = WORKLOAD
     head = args.precision + ("_ir" + ("64" if args.fp64_residuals else "")
                              if (args.precision != "fp64" and not args.no_refine) else
@@ -411,8 +490,10 @@ def run_ours(args):
                                   "on an i7-5820K incl. setup, manufactured right-hand side"},
     }
     forms = {}
+    u_forms = {head: main["u_host"]}
     for name in extra:
         r = run_form(stls, name, W, F, args, world)
+        u_forms[name] = r["u_host"]
         Sx, phx = r["S"], r["phases"]
         forms[name] = {"value": replica_rate(N, r["steps"], world, r["ms"]), "unit": "DoF/s",
                        "ms_per_step": r["ms"] / r["steps"], "steps": r["steps"],
@@ -427,7 +508,29 @@ def run_ours(args):
         torch.cuda.empty_cache()
     if forms:
         line["forms"] = forms
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if args.sweep:
+        # degree sweep at fixed N: the FD cost 4N(d n_s + n_t) stays flat in p, A x grows with 2p + 1
+        sweep = {}
+        for pp in range(2, 7):
+            for name in dict.fromkeys((head, "fp64_pcg")):
+                sweep["p%d_%s" % (pp, name)] = sweep_entry(stls, pp, name, F, args, world)
+                torch.cuda.empty_cache()
+        line["sweep"] = sweep
+    main["S"].close()
+    del F
+    torch.cuda.empty_cache()
+    if rank == 0 and world == 1 and not args.no_oracle_errors:
+        # the oracle's own solution (FP64 PCG to 1e-12 on the host cores), after every GPU timing
+        import numpy as np
+        u_ref, t_tol, k_tol, k_ref, t_setup = oracle_reference_solve(F_host)
+        nref = np.linalg.norm(u_ref)
+        line["errors_vs_oracle"] = {
+            "reference": "oracle FP64 PCG with the FD preconditioner to ||r|| / ||F|| <= 1e-12 "
+                         "(%d iterations)" % k_ref,
+            "rel_l2": {k: float(np.linalg.norm(v - u_ref) / nref) for k, v in u_forms.items()}}
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline_from_solve(u_ref.size, t_tol, k_tol, t_setup, FP64_ITERS)
+    elif rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample(F_host, FP64_ITERS)
     if rank == 0:
         print(json.dumps(line))
@@ -516,6 +619,10 @@ def main():
                     help="other forms timed in the same run (comma separated; empty for none)")
     ap.add_argument("--form-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sweep", dest="sweep", action="store_false",
+                    help="skip the degree sweep p = 2..6 at the workload's N")
+    ap.add_argument("--no-oracle-errors", action="store_true",
+                    help="skip the oracle's reference solve (errors of every form against it)")
     ap.add_argument("--oracle-iteration-sample", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.oracle_iteration_sample:  # child of single_thread_sample

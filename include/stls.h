@@ -47,11 +47,26 @@ enum stls_status {
   STLS_ENONFINITE = 6   /* a NaN or Inf appeared in the data or the iteration */
 };
 
-/* Arithmetic of the preconditioner's mode products (Algorithm 1, steps 2 and 4).
- * STLS_FP64: FP64 throughout.  STLS_MIXED_TF32 / STLS_MIXED_BF16: the mode
- * products run on the tensor cores with TF32 / BF16 operands and FP32
- * accumulation; the eigenvalue division, A x, the CG vectors and inner
- * products stay FP64.  The mixed forms should be used with flexible = 1. */
+/* Arithmetic of the preconditioner (Algorithm 1) and of the solve.
+ * STLS_FP64: FP64 throughout.
+ * STLS_MIXED_TF32 / STLS_MIXED_BF16: the mode products of steps 2 and 4 run
+ * on the tensor cores with TF32 / BF16 operands and FP32 accumulation; the
+ * tensors between products are stored in FP32 rounded to TF32 (TF32 form)
+ * or in BF16.  The eigenvalues are computed in FP64 on the host.  The
+ * division of step 3 runs in FP32: its divisor is the FP32 sum of lambda_t
+ * (rounded once from FP64) and of the spatial sum sum_k lambda_k[i_k]
+ * (formed in FP64 and rounded once), and the quotient is rounded to the
+ * operand format before the backward products; the FP32 division's error, a
+ * few units in the last FP32 place, is three orders of magnitude below that
+ * rounding.  The input r is rounded to FP32 and then to the operand format;
+ * z leaves as the FP32 accumulator (widened exactly to FP64 when the
+ * vectors are FP64).
+ * Where the rest of the solve runs in FP64 depends on `refine`: with
+ * refine = 0 (strict form), A x, the residual, every CG vector and every
+ * inner product are FP64; with refine = 1 only the outer residual F - A u
+ * (provisional steps in double-float arithmetic, see `refine`) and the
+ * correction of u are FP64, and the inner solve is FP32 as described there.
+ * The mixed forms should be used with flexible = 1. */
 enum stls_precision { STLS_FP64 = 0, STLS_MIXED_TF32 = 1, STLS_MIXED_BF16 = 2 };
 
 typedef struct {
@@ -69,10 +84,13 @@ typedef struct {
   int refine;       /* mixed forms only.  0: flexible CG in FP64 with the
                        tensor-core preconditioner.  1: iterative refinement:
                        an outer loop computes the residual r = F - A u in FP64
-                       and corrects u with an inner flexible CG in FP32
-                       (FP32 vectors and A p, tensor-core preconditioner, inner
-                       products compensated in FP32 per thread and summed in
-                       FP64) that reduces its scaled residual by inner_tol.  With d = 2, 3 an outer step whose
+                       and corrects u (in FP64) with an inner flexible CG in
+                       FP32: FP32 vectors x, r, p, q, z, FP32 A p, the
+                       tensor-core preconditioner on FP32 input and output,
+                       and inner products accumulated per thread in
+                       compensated FP32 (TwoProd and TwoSum, about twice the
+                       FP32 precision) and across threads in FP64; it reduces
+                       its scaled residual by inner_tol.  With d = 2, 3 an outer step whose
                        predicted residual ||r|| max(inner residual, 4e-4) exceeds
                        both 100 tol and 1e-8 takes a provisional residual with
                        the double-float A x (stls_apply_A_df); the FP64 residual
@@ -136,7 +154,7 @@ int stls_apply_A(stls_ctx *ctx, const double *x, double *y);
  * intermediate products stay inside the FP32 normal range (about 1e-38 to
  * 3e38 in magnitude).  x, y: device, B x N, must not overlap.  Errors:
  * STLS_EINVAL unless the context has refine = 1, d = 2 or 3 and degrees
- * 1..5 (the fused A x). */
+ * 1..6 (the fused A x). */
 int stls_apply_A_df(stls_ctx *ctx, const double *x, double *y);
 
 /* z = P^{-1} r for the batch by fast diagonalization (Eq. preconditioner,
@@ -247,11 +265,11 @@ int stls_phase_times(stls_ctx *ctx, double *ms_out4, long long *count_out4);
 int stls_phase_times_n(stls_ctx *ctx, int n, double *ms_out, long long *count_out);
 
 /* ---- allocation-free preconditioner apply ------------------------------------
- * The paper has no counterpart to this entry point; it serves callers that
- * cannot allocate device memory when they need the preconditioner: work being
- * recorded into a CUDA graph under stream capture (cudaMalloc cannot be
- * captured), real-time loops that cannot afford the allocator's latency or
- * its device synchronization, and plugin hosts that forbid allocation.
+ * The paper has no counterpart to this entry point.  It serves callers that
+ * cannot allocate device memory when they need the preconditioner: real-time
+ * loops that cannot afford the allocator's latency or the device
+ * synchronization that cudaMalloc and cudaFree can imply, and plugin hosts
+ * that give a component a fixed memory budget and forbid it to allocate.
  * Such callers cannot create a context either (stls_create allocates), so
  * every input comes from the caller.
  *
@@ -271,11 +289,14 @@ int stls_phase_times_n(stls_ctx *ctx, int n, double *ms_out, long long *count_ou
  *   stream   cudaStream_t (NULL = legacy default stream)
  * Nothing is allocated or freed.  The first call on a device looks up the
  * array's device address with cudaGetSymbolAddress (with that device
- * current); make that first call outside any stream capture.  All calls share
- * the array and nothing in it needs to start at zero; calls whose kernels
- * overlap on the GPU (different streams or threads) race on it and must be
- * serialized by the caller.  Errors: STLS_EINVAL (sizes, NULL pointers),
- * STLS_ECUDA (lookup or launch failure); text via stls_last_error(NULL). */
+ * current) and caches it with the device's context; make that first call
+ * before any stream capture.  After cudaDeviceReset the next call looks the
+ * address up again.  All calls share the array and nothing in it needs to
+ * start at zero; calls whose kernels overlap on the GPU (different streams or
+ * threads) race on it and must be serialized by the caller.  Errors:
+ * STLS_EINVAL (sizes, NULL pointers), STLS_ECUDA (lookup or launch failure,
+ * or a CUDA error already pending from earlier work, which is reported and
+ * left set); text via stls_last_error(NULL). */
 int stls_apply_precond_noalloc(int d, const int *n, int batch, const double *const *U,
                                const double *const *lam, const double *r, double *z,
                                void *cuda_stream);

@@ -55,8 +55,10 @@ class Solver:
     """Solver context for (0,1)^d x (0,T) with degree p splines and n_el elements.
 
     precision: "fp64" or the mixed forms "tf32" / "bf16" (tensor-core FD
-    mode products, FP64 elsewhere).  refine=True (mixed forms) solves by
-    iterative refinement: FP64 residuals F - A u, inner FP32 flexible CG.  Vectors are float64 CUDA tensors of
+    mode products with FP32 accumulation; FP32 division by the eigenvalue
+    sums; with refine=False every CG vector, A x and inner product in FP64).
+    refine=True (mixed forms) solves by iterative refinement: FP64 residuals
+    F - A u and corrections, inner FP32 flexible CG.  Vectors are float64 CUDA tensors of
     shape (batch, N) or (N,) for batch 1, in colexicographic order
     (direction 1 fastest, time slowest).
     """

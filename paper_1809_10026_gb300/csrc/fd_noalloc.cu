@@ -1,15 +1,14 @@
 // Allocation-free FP64 preconditioner apply (stls_apply_precond_noalloc).
 //
 // Some callers cannot allocate device memory at the point where they need the
-// preconditioner: code that records work into a CUDA graph while stream
-// capture is active (cudaMalloc is not a capturable operation), real-time
-// loops that must not pay for the allocator's latency or its implicit device
-// synchronization, and hosts that hand a plugin a fixed memory budget and
-// forbid it from allocating on its own.  They also may not be able to create
-// a solver context, since stls_create allocates.  For them this file offers
-// the FP64 fast-diagonalization solve z = P^{-1} r with every input supplied
-// by the caller and the two intermediate tensors kept in a file-scope device
-// array instead of allocated memory.
+// preconditioner: real-time loops that must not pay for the allocator's
+// latency or the device synchronization cudaMalloc and cudaFree can imply,
+// and hosts that hand a plugin a fixed memory budget and forbid it from
+// allocating on its own.  They may not be able to create a solver context
+// either, since stls_create allocates.  For them this file offers the FP64
+// fast-diagonalization solve z = P^{-1} r with every input supplied by the
+// caller and the two intermediate tensors kept in a file-scope device array
+// instead of allocated memory.
 //
 // The array is a fixed 8 MiB (2 x 2^19 doubles) that every GPU which loads
 // the library holds until the process exits.  One call handles at most
@@ -23,7 +22,11 @@
 // Host code cannot use the array's name as a device address (it denotes a
 // host-side shadow symbol), so the first call on each device looks up the
 // real address with cudaGetSymbolAddress while that device is current and
-// caches it.  That first call therefore must happen outside stream capture.
+// caches it together with the device's current context.  That first call
+// therefore must happen before any stream capture.  A later call that finds
+// another context current on the device (after cudaDeviceReset, which
+// reloads the module and may move the array) looks the address up again.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -46,6 +49,24 @@ static __device__ __align__(256) double g_noalloc_scratch[2 * kNoAllocMaxElems];
 
 std::mutex g_mutex;
 double *g_scratch_ptr[kMaxDevices] = {};
+CUcontext g_scratch_ctx[kMaxDevices] = {};
+
+// The driver's cuCtxGetCurrent through the runtime's entry-point query, so
+// that the library does not link libcuda directly.
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+CtxGetCurrentFn ctx_get_current() {
+  static CtxGetCurrentFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<CtxGetCurrentFn>(p);
+  }
+  return fn;
+}
 
 // out(o, i, c) = sum_j W(i, j) in(o, j, c) with W(i, j) = U[j][i] when
 // `transposed` (forward products, W = U^T) and U[i][j] otherwise.  When
@@ -158,7 +179,8 @@ cudaError_t launch_any(const double *in, double *out, const double *U, int trans
   }
 }
 
-// Device address of the scratch array on the current device (looked up once).
+// Device address of the scratch array on the current device, looked up once
+// per device and context.
 int scratch_for_current_device(double **out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
@@ -167,6 +189,13 @@ int scratch_for_current_device(double **out) {
     return STLS_ECUDA;
   }
   std::lock_guard<std::mutex> lock(g_mutex);
+  CUcontext ctx = nullptr;
+  if (g_scratch_ptr[dev] != nullptr) {
+    // cheap check that the context the address belongs to is still current
+    CtxGetCurrentFn get = ctx_get_current();
+    if (get != nullptr && get(&ctx) == CUDA_SUCCESS && ctx != nullptr && ctx != g_scratch_ctx[dev])
+      g_scratch_ptr[dev] = nullptr;
+  }
   if (g_scratch_ptr[dev] == nullptr) {
     void *p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
@@ -175,7 +204,11 @@ int scratch_for_current_device(double **out) {
                              cudaGetErrorString(e));
       return STLS_ECUDA;
     }
+    CtxGetCurrentFn get = ctx_get_current();
+    ctx = nullptr;
+    if (get != nullptr) get(&ctx);
     g_scratch_ptr[dev] = static_cast<double *>(p);
+    g_scratch_ctx[dev] = ctx;
   }
   *out = g_scratch_ptr[dev];
   return STLS_OK;
@@ -207,6 +240,14 @@ extern "C" int stls_apply_precond_noalloc(int d, const int *n, int batch, const 
   double *scratch = nullptr;
   int rc = scratch_for_current_device(&scratch);
   if (rc != STLS_OK) return rc;
+  // An error left pending by earlier work would be read back after our first
+  // launch and reported as ours: report it as what it is, and leave it set.
+  const cudaError_t pending = cudaPeekAtLastError();
+  if (pending != cudaSuccess) {
+    stls::set_thread_error(std::string("stls_apply_precond_noalloc: an earlier CUDA error is pending: ") +
+                           cudaGetErrorString(pending));
+    return STLS_ECUDA;
+  }
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   double *tmp[2] = {scratch, scratch + kNoAllocMaxElems};
   const int nprod = 2 * (d + 1);

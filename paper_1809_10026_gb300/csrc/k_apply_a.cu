@@ -636,6 +636,7 @@ cudaError_t dispatch_slice(int p, const SliceArgs<T> &a, cudaStream_t s) {
     case 3: return launch_slice_p<T, 3>(a, s);
     case 4: return launch_slice_p<T, 4>(a, s);
     case 5: return launch_slice_p<T, 5>(a, s);
+    case 6: return launch_slice_p<T, 6>(a, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -647,6 +648,7 @@ cudaError_t dispatch_zpass(int p, const ZArgs<T> &a, cudaStream_t s) {
     case 3: return launch_zpass_p<T, 3>(a, s);
     case 4: return launch_zpass_p<T, 4>(a, s);
     case 5: return launch_zpass_p<T, 5>(a, s);
+    case 6: return launch_zpass_p<T, 6>(a, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -658,6 +660,7 @@ cudaError_t dispatch_tpass(int p, const TArgs<T> &a, cudaStream_t s) {
     case 3: return launch_tpass_p<T, 3>(a, s);
     case 4: return launch_tpass_p<T, 4>(a, s);
     case 5: return launch_tpass_p<T, 5>(a, s);
+    case 6: return launch_tpass_p<T, 6>(a, s);
     default: return cudaErrorInvalidValue;
   }
 }

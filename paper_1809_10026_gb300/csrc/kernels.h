@@ -33,7 +33,7 @@ struct alignas(8) dfloat {
 // ---- fused A x for two and three spatial directions (k_apply_a.cu) -------------------
 // Band rows are padded to band_row_stride(p, sizeof(T)) elements (whole 16-byte
 // vectors); b2K holds 2 K exactly.
-constexpr int kFusedMaxP = 5;
+constexpr int kFusedMaxP = 6;
 int band_row_stride(int p, int elem_bytes);
 bool fused_A_supported(int d, int p_s, int p_t);
 

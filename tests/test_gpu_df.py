@@ -63,7 +63,9 @@ CASES = [dict(d=2, p=2, n_el=7), dict(d=2, p=3, n_el=9, T=1.3), dict(d=2, p=5, n
          dict(d=2, p=2, n_el=1), dict(d=3, p=5, n_el=1),
          dict(d=3, p=3, n_el=[4, 3, 5], T=1.1, p_t=1, n_el_t=7),
          dict(d=2, p=2, n_el=[6, 9], T=0.5, p_t=5, n_el_t=3),
-         dict(d=2, p=3, n_el=[40, 7])]
+         dict(d=2, p=3, n_el=[40, 7]),
+         dict(d=3, p=6, n_el=2), dict(d=2, p=6, n_el=[5, 3], T=0.8, p_t=6, n_el_t=2),
+         dict(d=2, p=2, n_el=4, p_t=6, n_el_t=3)]
 
 
 @pytest.mark.parametrize("case", CASES, ids=lambda c: "-".join(f"{k}{v}" for k, v in c.items()))

@@ -66,7 +66,10 @@ def test_apply_A_matches_oracle(d, p, n_el, T, batch):
 EDGE = [dict(d=2, p=2, n_el=1, T=1.0), dict(d=3, p=2, n_el=2, T=0.8),
         dict(d=2, p=4, n_el=1, T=1.0), dict(d=3, p=5, n_el=1, T=1.0),
         dict(d=3, p=3, n_el=[4, 3, 5], T=1.1, p_t=1, n_el_t=7),
-        dict(d=2, p=2, n_el=[6, 9], T=0.5, p_t=5, n_el_t=3)]
+        dict(d=2, p=2, n_el=[6, 9], T=0.5, p_t=5, n_el_t=3),
+        # degree 6 (the largest the fused kernels take): 13-point bands, wider than some directions
+        dict(d=3, p=6, n_el=2, T=1.0), dict(d=2, p=6, n_el=[5, 3], T=0.8),
+        dict(d=3, p=2, n_el=[3, 4, 2], T=1.0, p_t=6, n_el_t=3)]
 
 
 @pytest.mark.parametrize("case", EDGE, ids=lambda c: "-".join(f"{k}{v}" for k, v in c.items()))

@@ -1,7 +1,8 @@
 """GPU runs on the benchmark's mesh (3D, 64 elements per direction, 17 to
 20.5 million unknowns), checked by the oracle: Table 1's iteration counts of
-P + CG at n_sub = 64, and the benchmark's own solve (TF32 refinement form)
-with its residual recomputed by the oracle."""
+P + CG at n_sub = 64, the benchmark's own solve (TF32 refinement form) with
+its residual recomputed by the oracle, and the degree sweep at the
+benchmark's size (p = 2..6, 67 - p elements, N = 18,125,250 for every p)."""
 import numpy as np
 import pytest
 
@@ -55,3 +56,29 @@ def test_headline_solve_cube3d_p3_n64_tf32_refinement(fp64_residuals):
     u = u.cpu().numpy()
     res = np.linalg.norm(F - prob.apply_A_kron(u)) / np.linalg.norm(F)
     assert res <= 1e-8 + 1e-11 and abs(res - it["true_rel_res"]) <= 1e-11, (res, it)
+
+
+@pytest.mark.parametrize("p", [2, 3, 4, 5, 6])
+def test_degree_sweep_fixed_dofs(p):
+    """Degree sweep at fixed N = 18,125,250 (p = 2..6, 67 - p elements per
+    direction; F ~ U[-1,1], tol 1e-8): the headline form (TF32 refinement) and
+    the FP64 PCG converge, and the oracle's own A recomputes each returned
+    solution's residual.  Sec. 4.5: the FD cost does not depend on p, so the
+    FP64 PCG's iteration count stays in the range of Table 1 (12-13 on the
+    manufactured load; 17 here on the random one for p = 3)."""
+    n_el = 67 - p
+    prob = STProblem(3, p, n_el)
+    assert prob.N == 18125250
+    F = synth.uniform(prob.N, 4)
+    nF = np.linalg.norm(F)
+    Fg = torch.from_numpy(F).cuda()
+    for kw, max_iters in ((dict(precision="tf32", refine=True), 40), (dict(), 25)):
+        S = _solver(3, p, n_el, **kw)
+        u, info = S.solve(Fg, tol=1e-8, maxit=400)
+        it = info[0]
+        assert it["status"] == "ok" and it["true_rel_res"] <= 1e-8 and it["iters"] <= max_iters, (kw, it)
+        res = np.linalg.norm(F - prob.apply_A_kron(u.cpu().numpy())) / nF
+        print("p=%d %s: iterations %d (outer %d), residual %.3e (oracle %.3e)"
+              % (p, kw.get("precision", "fp64"), it["iters"], it["outer"], it["true_rel_res"], res))
+        assert res <= 1e-8 + 1e-11 and abs(res - it["true_rel_res"]) <= 1e-11, (kw, res, it)
+        del u, S

@@ -1,0 +1,203 @@
+"""Solutions of every solver form against the oracle's own solution.
+
+The oracle's reference solution comes from its own FP64 PCG with the fast
+diagonalization preconditioner (oracle.solve.pcg with oracle.fd.FD.apply and
+the Kronecker-factored A of Eq. A_kron), run to a residual far below the
+solver's; its agreement with the direct solve is pinned on reduced meshes by
+the CPU suite.  Compared here:
+
+* the FP64 PCG (solved to 1e-13 where the benchmark spec's bound is 1e-10);
+* the strict mixed forms (flexible CG with FP64 vectors and A x, tensor-core
+  preconditioner with TF32 or BF16 operands) and the refinement forms
+  (FP64 outer residual, FP32 inner flexible CG), solved to 1e-12, bound 1e-8;
+
+on the 3D workload with p = 4 and 32 elements per direction (1,375,640
+unknowns, manufactured load of Table 1) and on the benchmark's workload (p = 3,
+64 elements, 18,125,250 unknowns, F ~ U[-1,1]).  Every relative error is
+printed (run pytest with -s to see them), as is the error of the solve at
+the benchmark's tolerance 1e-8.
+
+At the solution the error is bounded by kappa(A) times the residual, and
+kappa(A) grows like h^-4; with both sides at a residual of 1e-12 to 1e-13 the
+errors measured on CPU models of these solves (oracle.mixed as the
+preconditioner) stay near 1e-13 on small meshes, so the bounds above are not
+near the rounding floor.
+
+The tensor-core preconditioner is also compared element by element with
+exact Algorithm 1: |z - z_exact| <= 2 * 2(d+1) * u_op * max|z_exact|, u_op the
+unit roundoff of the operand format (BF16 2^-9, TF32 2^-11): each of the
+2(d+1) mode products rounds its operands once, and the bound allows each one
+twice its unit roundoff relative to the largest entry (the CPU model of the
+roundings, oracle.mixed, stays within about half of it on these cases).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle.system import STProblem
+from oracle.fd import FD
+from oracle.solve import direct_solve, pcg
+from paper_1809_10026_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+PI = np.pi
+U_OP = {"bf16": 2.0 ** -9, "tf32": 2.0 ** -11}
+FORMS = [("tf32", False), ("bf16", False), ("tf32", True), ("bf16", True)]
+
+
+def _solver(*a, **k):
+    import paper_1809_10026_gb300 as stls
+    return stls.Solver(*a, **k)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _form_id(f):
+    return "%s_%s" % (f[0], "refine" if f[1] else "strict")
+
+
+def _oracle_reference(prob, F, tol):
+    fd = FD(prob)
+    u, its, hist = pcg(prob.apply_A_kron, fd.apply, F, tol, 400)
+    assert hist[-1] <= tol, hist[-1]
+    return u, its
+
+
+@pytest.fixture(scope="module")
+def cube3d_p4_n32():
+    """Table 1's load on the 3D mesh with p = 4 and 32 elements: the oracle's
+    PCG to 1e-13."""
+    prob = STProblem(3, 4, 32)
+    s = lambda x: np.sin(PI * x)
+    F = prob.load_separable([(1.0, np.cos, [s, s, s]), (3 * PI ** 2, np.sin, [s, s, s])])
+    u_ref, its = _oracle_reference(prob, F, 1e-13)
+    print("\ncube3d_p4_n32: oracle PCG to 1e-13 in %d iterations" % its)
+    return prob, F, u_ref
+
+
+@pytest.fixture(scope="module")
+def cube3d_p3_n64():
+    """The benchmark's workload: F ~ U[-1,1] (seed tag 4), the oracle's PCG to
+    1e-12 (about 25 iterations of the oracle on the host cores)."""
+    prob = STProblem(3, 3, 64)
+    F = synth.uniform(prob.N, 4)
+    u_ref, its = _oracle_reference(prob, F, 1e-12)
+    print("\ncube3d_p3_n64: oracle PCG to 1e-12 in %d iterations" % its)
+    return prob, F, u_ref
+
+
+def test_fp64_solve_cube3d_p4_n32_vs_oracle(cube3d_p4_n32):
+    prob, F, u_ref = cube3d_p4_n32
+    S = _solver(3, 4, 32)
+    Fg = torch.from_numpy(F).cuda()
+    u13, i13 = S.solve(Fg, tol=1e-13, maxit=400)
+    e13 = _rel(u13.cpu().numpy(), u_ref)
+    u8, i8 = S.solve(Fg, tol=1e-8, maxit=400)
+    e8 = _rel(u8.cpu().numpy(), u_ref)
+    print("cube3d_p4_n32 fp64: rel. error %.2e at tol 1e-13 (%d it), %.2e at tol 1e-8 (%d it)"
+          % (e13, i13[0]["iters"], e8, i8[0]["iters"]))
+    assert i13[0]["status"] == "ok" and e13 <= 1e-10
+    assert i8[0]["status"] == "ok" and i8[0]["true_rel_res"] <= 1e-8
+
+
+@pytest.mark.parametrize("form", FORMS, ids=_form_id)
+def test_mixed_solve_cube3d_p4_n32_vs_oracle(cube3d_p4_n32, form):
+    prec, refine = form
+    prob, F, u_ref = cube3d_p4_n32
+    S = _solver(3, 4, 32, precision=prec, refine=refine)
+    Fg = torch.from_numpy(F).cuda()
+    u12, i12 = S.solve(Fg, tol=1e-12, maxit=800)
+    e12 = _rel(u12.cpu().numpy(), u_ref)
+    u8, i8 = S.solve(Fg, tol=1e-8, maxit=400)
+    e8 = _rel(u8.cpu().numpy(), u_ref)
+    print("cube3d_p4_n32 %s: rel. error %.2e at tol 1e-12 (%d it), %.2e at tol 1e-8 (%d it, true res %.2e)"
+          % (_form_id(form), e12, i12[0]["iters"], e8, i8[0]["iters"], i8[0]["true_rel_res"]))
+    assert i12[0]["status"] == "ok" and e12 <= 1e-8
+    # the recursively updated residual of the strict form may sit slightly below the true one
+    assert i8[0]["status"] == "ok" and i8[0]["true_rel_res"] <= (1e-8 if refine else 1.5e-8)
+
+
+def test_fp64_solve_cube3d_p3_n64_vs_oracle(cube3d_p3_n64):
+    prob, F, u_ref = cube3d_p3_n64
+    S = _solver(3, 3, 64)
+    u, info = S.solve(torch.from_numpy(F).cuda(), tol=1e-12, maxit=400)
+    e = _rel(u.cpu().numpy(), u_ref)
+    print("cube3d_p3_n64 fp64: rel. error %.2e at tol 1e-12 (%d it)" % (e, info[0]["iters"]))
+    assert info[0]["status"] == "ok" and e <= 1e-10
+
+
+@pytest.mark.parametrize("form", FORMS, ids=_form_id)
+def test_mixed_solve_cube3d_p3_n64_vs_oracle(cube3d_p3_n64, form):
+    """The headline form (TF32 refinement) and the other mixed forms on the
+    benchmark's mesh, solved to 1e-12 and compared with the oracle's solution."""
+    prec, refine = form
+    prob, F, u_ref = cube3d_p3_n64
+    S = _solver(3, 3, 64, precision=prec, refine=refine)
+    Fg = torch.from_numpy(F).cuda()
+    u12, i12 = S.solve(Fg, tol=1e-12, maxit=800)
+    e12 = _rel(u12.cpu().numpy(), u_ref)
+    del u12
+    u8, i8 = S.solve(Fg, tol=1e-8, maxit=400)
+    e8 = _rel(u8.cpu().numpy(), u_ref)
+    print("cube3d_p3_n64 %s: rel. error %.2e at tol 1e-12 (%d it), %.2e at tol 1e-8 (%d it)"
+          % (_form_id(form), e12, i12[0]["iters"], e8, i8[0]["iters"]))
+    assert i12[0]["status"] == "ok" and e12 <= 1e-8
+    assert i8[0]["status"] == "ok" and i8[0]["true_rel_res"] <= (1e-8 if refine else 1.5e-8)
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+@pytest.mark.parametrize("d,p,n_el,batch", [(1, 2, 9, 2), (2, 3, 7, 3), (3, 2, 4, 2), (3, 3, 6, 1)])
+def test_strict_mixed_fcg_matches_direct_solve(prec, d, p, n_el, batch):
+    """Strict mixed form (refine = 0): flexible CG with FP64 vectors, FP64 A x and
+    the tensor-core preconditioner, to 1e-12, against the oracle's direct
+    solve.  CPU models of the same iteration reach ~3e-13 here."""
+    prob = STProblem(d, p, n_el)
+    A = prob.assemble_A_kron()
+    F = synth.uniform(prob.N, 77, batch=batch).reshape(batch, prob.N)
+    if batch > 1:
+        F[1] *= 1e-4
+    S = _solver(d, p, n_el, precision=prec, batch=batch)
+    u, info = S.solve(torch.from_numpy(F.reshape(-1) if batch == 1 else F).cuda(), tol=1e-12, maxit=500)
+    u = u.cpu().numpy().reshape(batch, prob.N)
+    for b in range(batch):
+        ref = direct_solve(A, F[b])
+        assert info[b]["status"] == "ok", info[b]
+        assert _rel(u[b], ref) <= 1e-10, (b, _rel(u[b], ref))
+
+
+TC_CASES = [(1, 2, 7, 1), (2, 3, 6, 3), (2, 5, 9, 1), (3, 2, 4, 2), (3, 3, 9, 1), (3, 4, 12, 1),
+            (2, 2, 70, 2), (3, 3, 20, 2), (3, 2, 1, 1)]
+
+
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+@pytest.mark.parametrize("d,p,n_el,batch", TC_CASES)
+def test_tc_precond_elementwise_vs_exact(prec, d, p, n_el, batch):
+    """Every entry of the tensor-core apply (boundary fibers, ragged tiles and
+    batches included) within 2 * 2(d+1) * u_op of max|z| of exact Algorithm 1."""
+    prob = STProblem(d, p, n_el)
+    fd = FD(prob)
+    S = _solver(d, p, n_el, precision=prec, batch=batch)
+    r = synth.uniform(prob.N, 500 + d + p, batch=batch).reshape(batch, prob.N)
+    z = S.apply_precond(torch.from_numpy(r.reshape(-1) if batch == 1 else r).cuda()).cpu().numpy()
+    z = z.reshape(batch, prob.N)
+    c = 2 * 2 * (d + 1) * U_OP[prec]
+    for b in range(batch):
+        ex = fd.apply(r[b])
+        err = np.abs(z[b] - ex).max() / np.abs(ex).max()
+        assert err <= c, (b, err, c)
+
+
+def test_tc_precond_elementwise_vs_exact_cube3d_p3_n64():
+    """The benchmark's mesh, TF32 form: element-wise bound on all 18,125,250 entries."""
+    prob = STProblem(3, 3, 64)
+    fd = FD(prob)
+    S = _solver(3, 3, 64, precision="tf32")
+    r = synth.uniform(prob.N, 4)
+    z = S.apply_precond(torch.from_numpy(r).cuda()).cpu().numpy()
+    ex = fd.apply(r)
+    err = np.abs(z - ex).max() / np.abs(ex).max()
+    assert err <= 2 * 2 * 4 * U_OP["tf32"], err

@@ -1,10 +1,12 @@
 """The allocation-free preconditioner apply (stls_apply_precond_noalloc).
 
 It exists for callers that cannot allocate device memory where they apply
-the preconditioner (graph capture, real-time loops, allocation-free plugin
-hosts): its scratch is a fixed array inside the library.  This file checks,
-through the C ABI, that two calls in a row agree with stls_apply_precond of a
-solver context (FP64 form) to the tolerance the FD parity tests use, and that
+the preconditioner (real-time loops that cannot afford the allocator, plugin
+hosts with a fixed memory budget): its scratch is a fixed array inside the
+library.  This file checks, through the C ABI, that two calls in a row agree
+with the oracle's fast-diagonalization solve (Algorithm 1) and with
+stls_apply_precond of a solver context (FP64 form), both to the tolerance the
+FD parity tests use, for one, two and three space dimensions, and that
 oversized requests are refused before any launch.  It is named so pytest
 collects it last.
 """
@@ -16,6 +18,8 @@ import pytest
 torch = pytest.importorskip("torch")
 
 import paper_1809_10026_gb300 as stls
+from oracle.fd import FD
+from oracle.system import STProblem
 from paper_1809_10026_gb300 import _lib, synth
 
 pytestmark = pytest.mark.gpu
@@ -43,9 +47,10 @@ def _call(d, sizes, batch, U_dev, lam_dev, r, z):
                                           ctypes.c_void_p(z.data_ptr()), ctypes.c_void_p(stream))
 
 
-@pytest.mark.parametrize("d,p,n_el,batch", [(2, 3, 64, 1), (3, 3, 9, 2)])
-def test_noalloc_matches_context_apply_twice(d, p, n_el, batch):
+@pytest.mark.parametrize("d,p,n_el,batch", [(1, 2, 16, 3), (2, 3, 64, 1), (3, 3, 9, 2)])
+def test_noalloc_matches_oracle_and_context_apply_twice(d, p, n_el, batch):
     S = stls.Solver(d, p, n_el, batch=batch)
+    fd = FD(STProblem(d, p, n_el))
     U, lam = _factors(d, p, n_el)
     U_dev = [torch.from_numpy(np.ascontiguousarray(u)).cuda() for u in U]
     lam_dev = [torch.from_numpy(l).cuda() for l in lam]
@@ -57,7 +62,12 @@ def test_noalloc_matches_context_apply_twice(d, p, n_el, batch):
         assert _call(d, sizes, batch, U_dev, lam_dev, r, z) == _lib.STLS_OK
         ref = S.apply_precond(r)
         torch.cuda.synchronize()
-        zr, rr = z.cpu().numpy(), ref.cpu().numpy()
+        zr = z.cpu().numpy().reshape(batch, S.N)
+        rr = ref.cpu().numpy().reshape(batch, S.N)
+        rh = r.cpu().numpy().reshape(batch, S.N)
+        for b in range(batch):
+            ex = fd.apply(rh[b])
+            np.testing.assert_allclose(zr[b], ex, rtol=0, atol=tol * np.abs(ex).max())
         np.testing.assert_allclose(zr, rr, rtol=0, atol=tol * np.abs(rr).max())
 
 
