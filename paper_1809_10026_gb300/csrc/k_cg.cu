@@ -17,6 +17,15 @@ namespace stls {
 namespace {
 
 constexpr int kThreads = 256;
+// Grid-stride loops handle kU entries per trip, S apart: every load of the
+// trip is issued before any of them is used, so that a thread keeps kU loads
+// of each vector in flight (a streaming kernel needs about 45 GB/s per SM,
+// i.e. tens of KB in flight).  The entries are still visited, and summed, in
+// the order i0, i0 + S, i0 + 2S, ..., so results do not depend on kU.
+constexpr int kU = 4;
+// Resident blocks per SM the kernels are compiled for (64 registers a thread:
+// room for the kU loads of up to four vectors).
+constexpr int kBlocksPerSM = 4;
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -76,19 +85,29 @@ __device__ bool grid_sum(double (&v)[NV], RedWork rw, int b, double (&tot)[NV]) 
   return true;
 }
 
-__global__ void __launch_bounds__(kThreads, 8)
+__global__ void __launch_bounds__(kThreads, kBlocksPerSM)
     cg_init_kernel(const double *__restrict__ F, double *__restrict__ x, double *__restrict__ r,
                    long long N, CGState *st, RedWork rw) {
   const int b = blockIdx.y;
   const double *Fb = F + static_cast<size_t>(b) * N;
   double *xb = x + static_cast<size_t>(b) * N, *rb = r + static_cast<size_t>(b) * N;
   double v[1] = {0.0};
-  for (long long i = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x; i < N;
-       i += static_cast<long long>(gridDim.x) * kThreads) {
-    double f = Fb[i];
-    xb[i] = 0.0;
-    rb[i] = f;
-    v[0] = fma(f, f, v[0]);
+  const long long i0 = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x;
+  const long long S = static_cast<long long>(gridDim.x) * kThreads;
+  for (long long i = i0; i < N; i += kU * S) {
+    double f[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u)
+      if (i + u * S < N) f[u] = Fb[i + u * S];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const long long j = i + u * S;
+      if (j < N) {
+        xb[j] = 0.0;
+        rb[j] = f[u];
+        v[0] = fma(f[u], f[u], v[0]);
+      }
+    }
   }
   double tot[1];
   if (grid_sum<1>(v, rw, b, tot) && threadIdx.x == 0) {
@@ -113,7 +132,7 @@ __global__ void __launch_bounds__(kThreads, 8)
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads, 8)
+__global__ void __launch_bounds__(kThreads, kBlocksPerSM)
     cg_alpha_kernel(const T *__restrict__ p, const T *__restrict__ q, long long N,
                     CGState *st, RedWork rw) {
   const int b = blockIdx.y;
@@ -179,11 +198,11 @@ struct PadIter {
   }
 };
 
-// (8 blocks of 256 threads per SM: the reduction grid is sized for that)
+// (kBlocksPerSM blocks of 256 threads per SM: the reduction grid is sized for that)
 // DEFER: x += alpha p is left to the next p update (launch_cg_p with x), or to
 // launch_cg_x_pending once the loop ends; xpend records that it is owed.
 template <typename T, bool PAD = false, bool DEFER = false>
-__global__ void __launch_bounds__(kThreads, 8)
+__global__ void __launch_bounds__(kThreads, kBlocksPerSM)
     cg_xr_kernel(T *__restrict__ x, T *__restrict__ r, const T *__restrict__ p,
                  const T *__restrict__ q, long long N, double tol, CGState *st, RedWork rw, PadOut pad = {}) {
   const int b = blockIdx.y;
@@ -193,30 +212,65 @@ __global__ void __launch_bounds__(kThreads, 8)
   const T *pb = p + static_cast<size_t>(b) * N, *qb = q + static_cast<size_t>(b) * N;
   double v[1] = {0.0};
   if (active) {
+    const long long i0 = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x;
+    const long long S = static_cast<long long>(gridDim.x) * kThreads;
     if constexpr (sizeof(T) == 4) {
       Dot2f acc;
-      const long long i0 = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x;
-      const long long S = static_cast<long long>(gridDim.x) * kThreads;
       PadIter it(i0, S, PAD ? pad : PadOut{nullptr, 1, 1});
       float *pb_out = PAD ? pad.out + static_cast<size_t>(b) * (N / pad.n) * pad.np : nullptr;
-      for (long long i = i0; i < N; i += S) {
-        if (!DEFER) xb[i] = fma(alpha, pb[i], xb[i]);
-        const T ri = fma(-alpha, qb[i], rb[i]);
-        rb[i] = ri;
-        acc.add(ri, ri);
-        if (PAD) {
-          pb_out[it.off] = ptx::tf32_rna(ri);
-          it.next();
+      for (long long i = i0; i < N; i += kU * S) {
+        T xv[kU], pv[kU], qv[kU], rv[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+          const long long j = i + u * S;
+          if (j < N) {
+            if (!DEFER) {
+              xv[u] = xb[j];
+              pv[u] = pb[j];
+            }
+            qv[u] = qb[j];
+            rv[u] = rb[j];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+          const long long j = i + u * S;
+          if (j < N) {
+            if (!DEFER) xb[j] = fma(alpha, pv[u], xv[u]);
+            const T ri = fma(-alpha, qv[u], rv[u]);
+            rb[j] = ri;
+            acc.add(ri, ri);
+            if (PAD) {
+              pb_out[it.off] = ptx::tf32_rna(ri);
+              it.next();
+            }
+          }
         }
       }
       v[0] = acc.value();
     } else {
-      for (long long i = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x; i < N;
-           i += static_cast<long long>(gridDim.x) * kThreads) {
-        xb[i] = fma(alpha, pb[i], xb[i]);
-        const T ri = fma(-alpha, qb[i], rb[i]);
-        rb[i] = ri;
-        v[0] = fma(static_cast<double>(ri), static_cast<double>(ri), v[0]);
+      for (long long i = i0; i < N; i += kU * S) {
+        T xv[kU], pv[kU], qv[kU], rv[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+          const long long j = i + u * S;
+          if (j < N) {
+            xv[u] = xb[j];
+            pv[u] = pb[j];
+            qv[u] = qb[j];
+            rv[u] = rb[j];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+          const long long j = i + u * S;
+          if (j < N) {
+            xb[j] = fma(alpha, pv[u], xv[u]);
+            const T ri = fma(-alpha, qv[u], rv[u]);
+            rb[j] = ri;
+            v[0] = fma(static_cast<double>(ri), static_cast<double>(ri), v[0]);
+          }
+        }
       }
     }
   }
@@ -238,7 +292,7 @@ __global__ void __launch_bounds__(kThreads, 8)
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads, 8)
+__global__ void __launch_bounds__(kThreads, kBlocksPerSM)
     cg_beta_kernel(const T *__restrict__ z, const T *__restrict__ r,
                    const T *__restrict__ q, long long N, int flexible, int first, CGState *st,
                    RedWork rw) {
@@ -247,22 +301,49 @@ __global__ void __launch_bounds__(kThreads, 8)
   const T *qb = q + static_cast<size_t>(b) * N;
   const bool need_zq = flexible && !first;
   double v[2] = {0.0, 0.0};
+  const long long i0 = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x;
+  const long long S = static_cast<long long>(gridDim.x) * kThreads;
   if constexpr (sizeof(T) == 4) {
     Dot2f zr, zq;
-    for (long long i = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x; i < N;
-         i += static_cast<long long>(gridDim.x) * kThreads) {
-      const T zi = zb[i];
-      zr.add(zi, rb[i]);
-      if (need_zq) zq.add(zi, qb[i]);
+    for (long long i = i0; i < N; i += kU * S) {
+      T zv[kU], rv[kU], qv[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const long long j = i + u * S;
+        if (j < N) {
+          zv[u] = zb[j];
+          rv[u] = rb[j];
+          if (need_zq) qv[u] = qb[j];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u)
+        if (i + u * S < N) {
+          zr.add(zv[u], rv[u]);
+          if (need_zq) zq.add(zv[u], qv[u]);
+        }
     }
     v[0] = zr.value();
     v[1] = zq.value();
   } else {
-    for (long long i = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x; i < N;
-         i += static_cast<long long>(gridDim.x) * kThreads) {
-      const double zi = static_cast<double>(zb[i]);
-      v[0] = fma(zi, static_cast<double>(rb[i]), v[0]);
-      if (need_zq) v[1] = fma(zi, static_cast<double>(qb[i]), v[1]);
+    for (long long i = i0; i < N; i += kU * S) {
+      T zv[kU], rv[kU], qv[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const long long j = i + u * S;
+        if (j < N) {
+          zv[u] = zb[j];
+          rv[u] = rb[j];
+          if (need_zq) qv[u] = qb[j];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u)
+        if (i + u * S < N) {
+          const double zi = static_cast<double>(zv[u]);
+          v[0] = fma(zi, static_cast<double>(rv[u]), v[0]);
+          if (need_zq) v[1] = fma(zi, static_cast<double>(qv[u]), v[1]);
+        }
     }
   }
   double tot[2];
@@ -293,7 +374,7 @@ __global__ void __launch_bounds__(kThreads, 8)
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads, 8)
+__global__ void __launch_bounds__(kThreads, kBlocksPerSM)
     cg_p_kernel(const T *__restrict__ z, T *__restrict__ p, long long N, int first,
                 CGState *st, T *__restrict__ x, unsigned *tickets) {
   const int b = blockIdx.y;
@@ -305,11 +386,27 @@ __global__ void __launch_bounds__(kThreads, 8)
     // the x update deferred by cg_xr: x += alpha p with the p it used
     const T alpha = static_cast<T>(st[b].alpha);
     T *xb = x + static_cast<size_t>(b) * N;
-    for (long long i = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x; i < N;
-         i += static_cast<long long>(gridDim.x) * kThreads) {
-      const T po = pb[i];
-      xb[i] = fma(alpha, po, xb[i]);
-      pb[i] = fma(beta, po, zb[i]);
+    const long long i0 = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x;
+    const long long S = static_cast<long long>(gridDim.x) * kThreads;
+    for (long long i = i0; i < N; i += kU * S) {
+      T pv[kU], xv[kU], zv[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const long long j = i + u * S;
+        if (j < N) {
+          pv[u] = pb[j];
+          xv[u] = xb[j];
+          zv[u] = zb[j];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const long long j = i + u * S;
+        if (j < N) {
+          xb[j] = fma(alpha, pv[u], xv[u]);
+          pb[j] = fma(beta, pv[u], zv[u]);
+        }
+      }
     }
     // the last block clears the flag (every block has read the state by then)
     __shared__ bool is_last;
@@ -325,15 +422,30 @@ __global__ void __launch_bounds__(kThreads, 8)
     }
     return;
   }
-  for (long long i = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x; i < N;
-       i += static_cast<long long>(gridDim.x) * kThreads)
-    pb[i] = first ? zb[i] : fma(beta, pb[i], zb[i]);
+  const long long i0 = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x;
+  const long long S = static_cast<long long>(gridDim.x) * kThreads;
+  for (long long i = i0; i < N; i += kU * S) {
+    T pv[kU], zv[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const long long j = i + u * S;
+      if (j < N) {
+        zv[u] = zb[j];
+        if (!first) pv[u] = pb[j];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const long long j = i + u * S;
+      if (j < N) pb[j] = first ? zv[u] : fma(beta, pv[u], zv[u]);
+    }
+  }
 }
 
 // x += alpha p for the right-hand sides whose deferred update is still owed
 // (xpend) when the CG loop ends.
 template <typename T>
-__global__ void __launch_bounds__(kThreads, 8)
+__global__ void __launch_bounds__(kThreads, kBlocksPerSM)
     cg_x_pending_kernel(T *__restrict__ x, const T *__restrict__ p, long long N, const CGState *st) {
   const int b = blockIdx.y;
   if (!st[b].xpend) return;
@@ -345,7 +457,7 @@ __global__ void __launch_bounds__(kThreads, 8)
     xb[i] = fma(alpha, pb[i], xb[i]);
 }
 
-__global__ void __launch_bounds__(kThreads, 8)
+__global__ void __launch_bounds__(kThreads, kBlocksPerSM)
     true_residual_kernel(const double *__restrict__ F, const double *__restrict__ Ax, long long N,
                          CGState *st, RedWork rw) {
   const int b = blockIdx.y;
@@ -365,7 +477,7 @@ __global__ void __launch_bounds__(kThreads, 8)
 // exact and done on the exponent field), d = 0, and the inner CG state for it
 // (active where the outer solve is active).  No FP64 arithmetic per entry: the
 // norm is accumulated by Dot2f.
-__global__ void __launch_bounds__(kThreads, 8)
+__global__ void __launch_bounds__(kThreads, kBlocksPerSM)
     ir_start_kernel(const double *__restrict__ r64, float *__restrict__ r32, float *__restrict__ d,
                     long long N, const CGState *outer, CGState *inner, RedWork rw, PadOut pad) {
   const int b = blockIdx.y;
@@ -378,14 +490,24 @@ __global__ void __launch_bounds__(kThreads, 8)
   const bool padded = pad.out != nullptr;
   PadIter it(i0, S, padded ? pad : PadOut{nullptr, 1, 1});
   float *pb_out = padded ? pad.out + static_cast<size_t>(b) * (N / pad.n) * pad.np : nullptr;
-  for (long long i = i0; i < N; i += S) {
-    const float x = ptx::f64_to_f32_rn(ptx::scale_f64(rb[i], -k));
-    ib[i] = x;
-    db[i] = 0.f;
-    acc.add(x, x);
-    if (padded) {
-      pb_out[it.off] = ptx::tf32_rna(x);
-      it.next();
+  for (long long i = i0; i < N; i += kU * S) {
+    double rv[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u)
+      if (i + u * S < N) rv[u] = rb[i + u * S];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const long long j = i + u * S;
+      if (j < N) {
+        const float x = ptx::f64_to_f32_rn(ptx::scale_f64(rv[u], -k));
+        ib[j] = x;
+        db[j] = 0.f;
+        acc.add(x, x);
+        if (padded) {
+          pb_out[it.off] = ptx::tf32_rna(x);
+          it.next();
+        }
+      }
     }
   }
   double v[1] = {acc.value()};
@@ -407,7 +529,7 @@ __global__ void __launch_bounds__(kThreads, 8)
 // whose outer solve is active; one FP64 add per entry.  With udf != NULL also
 // the double-float image of the new u (launch_df_split's, scaled by the
 // exponent of ||F||), for every right-hand side.
-__global__ void __launch_bounds__(kThreads, 8)
+__global__ void __launch_bounds__(kThreads, kBlocksPerSM)
     ir_correct_kernel(double *__restrict__ u, const float *__restrict__ d, dfloat *__restrict__ udf, long long N,
                       const CGState *outer) {
   const int b = blockIdx.y;
@@ -417,37 +539,69 @@ __global__ void __launch_bounds__(kThreads, 8)
   double *ub = u + static_cast<size_t>(b) * N;
   const float *db = d + static_cast<size_t>(b) * N;
   dfloat *yb = udf != nullptr ? udf + static_cast<size_t>(b) * N : nullptr;
-  for (long long i = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x; i < N;
-       i += static_cast<long long>(gridDim.x) * kThreads) {
-    double v = ub[i];
-    if (active) {
-      v += ptx::scale_f64(ptx::f32_to_f64(db[i]), k);
-      ub[i] = v;
+  const long long i0 = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x;
+  const long long S = static_cast<long long>(gridDim.x) * kThreads;
+  for (long long i = i0; i < N; i += kU * S) {
+    double uv[kU];
+    float dv[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const long long j = i + u * S;
+      if (j < N) {
+        uv[u] = ub[j];
+        if (active) dv[u] = db[j];
+      }
     }
-    if (yb != nullptr) {
-      const double w = ptx::scale_f64(v, -kF);
-      dfloat o;
-      o.h = ptx::f64_to_f32_rn(w);
-      o.l = ptx::f64_to_f32_rn(w - ptx::f32_to_f64(o.h));
-      yb[i] = o;
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const long long j = i + u * S;
+      if (j >= N) continue;
+      double v = uv[u];
+      if (active) {
+        v += ptx::scale_f64(ptx::f32_to_f64(dv[u]), k);
+        ub[j] = v;
+      }
+      if (yb != nullptr) {
+        const double w = ptx::scale_f64(v, -kF);
+        dfloat o;
+        o.h = ptx::f64_to_f32_rn(w);
+        o.l = ptx::f64_to_f32_rn(w - ptx::f32_to_f64(o.h));
+        yb[j] = o;
+      }
     }
   }
 }
 
 // r64 = F - A u in FP64 and the outer convergence test on ||r64|| / ||F||
 // (`count`: whether this residual ends an outer step).
-__global__ void __launch_bounds__(kThreads, 8)
+__global__ void __launch_bounds__(kThreads, kBlocksPerSM)
     ir_residual_kernel(const double *__restrict__ F, const double *__restrict__ Au, double *__restrict__ r64,
                        long long N, double tol, int count, CGState *outer, RedWork rw) {
   const int b = blockIdx.y;
   const double *Fb = F + static_cast<size_t>(b) * N, *Ab = Au + static_cast<size_t>(b) * N;
   double *rb = r64 + static_cast<size_t>(b) * N;
   double v[1] = {0.0};
-  for (long long i = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x; i < N;
-       i += static_cast<long long>(gridDim.x) * kThreads) {
-    const double e = Fb[i] - Ab[i];
-    rb[i] = e;
-    v[0] = fma(e, e, v[0]);
+  const long long i0 = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x;
+  const long long S = static_cast<long long>(gridDim.x) * kThreads;
+  for (long long i = i0; i < N; i += kU * S) {
+    double fv[kU], av[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const long long j = i + u * S;
+      if (j < N) {
+        fv[u] = Fb[j];
+        av[u] = Ab[j];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const long long j = i + u * S;
+      if (j < N) {
+        const double e = fv[u] - av[u];
+        rb[j] = e;
+        v[0] = fma(e, e, v[0]);
+      }
+    }
   }
   double tot[1];
   if (grid_sum<1>(v, rw, b, tot) && threadIdx.x == 0) {
@@ -469,7 +623,7 @@ __global__ void __launch_bounds__(kThreads, 8)
 // r64 = F - 2^k (h + l) for the double-float image h + l of 2^-k A u, in
 // FP64 (the FP32 parts are widened and scaled exactly by integer operations),
 // and its norm; provisional: no convergence test, no status change.
-__global__ void __launch_bounds__(kThreads, 8)
+__global__ void __launch_bounds__(kThreads, kBlocksPerSM)
     ir_residual_df_kernel(const double *__restrict__ F, const dfloat *__restrict__ Au, double *__restrict__ r64,
                           long long N, CGState *outer, RedWork rw) {
   const int b = blockIdx.y;
@@ -478,12 +632,29 @@ __global__ void __launch_bounds__(kThreads, 8)
   const dfloat *Ab = Au + static_cast<size_t>(b) * N;
   double *rb = r64 + static_cast<size_t>(b) * N;
   double v[1] = {0.0};
-  for (long long i = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x; i < N;
-       i += static_cast<long long>(gridDim.x) * kThreads) {
-    const dfloat a = Ab[i];
-    const double e = (Fb[i] - ptx::scale_f64(ptx::f32_to_f64(a.h), k)) - ptx::scale_f64(ptx::f32_to_f64(a.l), k);
-    rb[i] = e;
-    v[0] = fma(e, e, v[0]);
+  const long long i0 = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x;
+  const long long S = static_cast<long long>(gridDim.x) * kThreads;
+  for (long long i = i0; i < N; i += kU * S) {
+    double fv[kU];
+    dfloat av[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const long long j = i + u * S;
+      if (j < N) {
+        fv[u] = Fb[j];
+        av[u] = Ab[j];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const long long j = i + u * S;
+      if (j < N) {
+        const dfloat a = av[u];
+        const double e = (fv[u] - ptx::scale_f64(ptx::f32_to_f64(a.h), k)) - ptx::scale_f64(ptx::f32_to_f64(a.l), k);
+        rb[j] = e;
+        v[0] = fma(e, e, v[0]);
+      }
+    }
   }
   double tot[1];
   if (grid_sum<1>(v, rw, b, tot) && threadIdx.x == 0) {
@@ -546,8 +717,13 @@ unsigned grid_1d(long long n) {
 }  // namespace
 
 int red_grid_for(long long n) {
-  long long g = (n + kThreads * 8 - 1) / (kThreads * 8);
-  if (g > 1216) g = 1216;  // 8 blocks of 256 threads on each of the 152 SMs
+  // one wave of the reduction kernels: kBlocksPerSM blocks on every SM of the current device
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    sms = 152;
+  const long long cap = static_cast<long long>(kBlocksPerSM) * sms;
+  long long g = (n + kThreads * kU - 1) / (kThreads * kU);
+  if (g > cap) g = cap;
   return static_cast<int>(g < 1 ? 1 : g);
 }
 
