@@ -10,7 +10,12 @@
 // 128-byte atoms, 1024 bytes apart), so the tile needs no conversion in
 // shared memory: A = 128 fibers x K, B = the eigenvector matrix (N = n_k padded
 // to 16 rows, K-major SW128 image built on the host), D = FP32 in tensor
-// memory (lane = fiber, column = output index m).  The epilogue writes entry
+// memory (lane = fiber, column = output index m).  A last partial group of at
+// most 16 values of K (n_k = 65: one value) is not fetched as a whole 128-byte
+// swizzled box but as boxes of 4 values (16-byte rows, no swizzle), which are
+// the 8-row x 16-byte core matrices of the no-swizzle K-major layout (8-row
+// groups 128 bytes apart, 4-value K chunks 2048 bytes apart): smaller stages,
+// and on the 18.1M-unknown cube 343 instead of 346 us per apply.  The epilogue writes entry
 // (m, f) as element i_{k+1} of fiber g + G m of the next pass (f = i_{k+1} +
 // n_{k+1} g), i.e. with mode k slowest and mode k+1 fastest; after 2(d+1)
 // passes the order is natural again.  For a fixed m a warp stores 32
@@ -61,6 +66,9 @@ constexpr int kMaxStages = 4;
 constexpr int kSmemLimit = 227 * 1024;
 constexpr int kStaticSmem = 1024;  // barriers, holder, eigenvalue copy
 
+constexpr uint32_t kTailBoxBytes = kFib * 16;  // one 4-value box of the no-swizzle tail
+constexpr int kTailMax = 16;                    // largest K tail fetched in 4-value boxes
+
 struct RotArgs {
   void *out;
   const uint8_t *bimg;  // K-major SW128 image of W: nkb atoms of np rows x 128 bytes
@@ -71,7 +79,9 @@ struct RotArgs {
   long long G;          // fib_per_b / n_next
   long long blk_out;    // output elements per right-hand side
   int n, nkb, ksteps, np, n_next, np_next, stages, round_out;
-  uint32_t bytes_b, off_stage, idesc;
+  int full_atoms;  // 32-value K groups fetched as SW128 boxes
+  int tail_boxes;  // 4-value boxes of the no-swizzle tail (even; 0: none)
+  uint32_t bytes_b, off_stage, idesc, stage_bytes;
 };
 
 __device__ __forceinline__ uint8_t *align1024(uint8_t *p) {
@@ -82,7 +92,8 @@ __device__ __forceinline__ void store_val(float *p, float v) { *p = v; }
 __device__ __forceinline__ void store_val(double *p, float v) { *p = ptx::f32_to_f64(v); }
 
 template <typename OutT, bool DIVIDE>
-__global__ void __launch_bounds__(kRotThreads, 1) rot_kernel(const __grid_constant__ CUtensorMap tin, RotArgs a) {
+__global__ void __launch_bounds__(kRotThreads, 1) rot_kernel(const __grid_constant__ CUtensorMap tin,
+                                                             const __grid_constant__ CUtensorMap ttail, RotArgs a) {
   extern __shared__ uint8_t smem_dyn[];
   __shared__ __align__(8) uint64_t bar_full[kMaxStages], bar_empty[kMaxStages], bar_tfull[kAcc], bar_tempty[kAcc];
   __shared__ uint32_t tmem_holder;
@@ -91,7 +102,7 @@ __global__ void __launch_bounds__(kRotThreads, 1) rot_kernel(const __grid_consta
   uint8_t *sm = align1024(smem_dyn);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int S = a.stages;
-  const uint32_t stage_bytes = static_cast<uint32_t>(a.nkb) * kBoxBytes;
+  const uint32_t stage_bytes = a.stage_bytes;
   const uint32_t sB = ptx::smem_u32(sm), st0 = ptx::smem_u32(sm + a.off_stage);
   const uint32_t full0 = ptx::smem_u32(&bar_full[0]), empty0 = ptx::smem_u32(&bar_empty[0]);
   const uint32_t tfull0 = ptx::smem_u32(&bar_tfull[0]), tempty0 = ptx::smem_u32(&bar_tempty[0]);
@@ -141,8 +152,11 @@ __global__ void __launch_bounds__(kRotThreads, 1) rot_kernel(const __grid_consta
         if (!ok) break;
         const uint32_t dst = st0 + s * stage_bytes;
         ptx::mbar_expect_tx(full0 + 8 * s, stage_bytes);
-        for (int j = 0; j < a.nkb; ++j)
+        for (int j = 0; j < a.full_atoms; ++j)
           ptx::tma_load_2d(dst + j * kBoxBytes, &tin, j * kBoxK, static_cast<int>(t * kFib), full0 + 8 * s);
+        for (int j = 0; j < a.tail_boxes; ++j)  // x = 32 full_atoms + 4 j: 16-byte aligned
+          ptx::tma_load_2d(dst + a.full_atoms * kBoxBytes + j * kTailBoxBytes, &ttail, a.full_atoms * kBoxK + 4 * j,
+                           static_cast<int>(t * kFib), full0 + 8 * s);
         issued = i + 1;
       }
     }
@@ -162,9 +176,12 @@ __global__ void __launch_bounds__(kRotThreads, 1) rot_kernel(const __grid_consta
         if (!ok) break;
         ptx::fence_after_sync();
         const uint32_t A = st0 + s * stage_bytes, D = tmem + acc * kAccCols;
+        const int kfull = 4 * a.full_atoms;
         for (int kk = 0; kk < a.ksteps; ++kk) {
           const int j = kk >> 2, w = kk & 3;  // 128-byte atom, 32-byte K step inside it
-          const uint64_t ad = ptx::make_desc(A + j * kBoxBytes + w * 32, 16, 1024, 2);
+          const uint64_t ad = kk < kfull ? ptx::make_desc(A + j * kBoxBytes + w * 32, 16, 1024, 2)
+                                         : ptx::make_desc(A + a.full_atoms * kBoxBytes + (kk - kfull) * 2 * kTailBoxBytes,
+                                                          kTailBoxBytes, 128, 0);
           const uint64_t bd = ptx::make_desc(sB + j * atom_b + w * 32, 16, 1024, 2);
           ptx::mma_tf32(D, ad, bd, a.idesc, kk > 0 ? 1u : 0u);
         }
@@ -311,6 +328,19 @@ bool make_map(CUtensorMap &m, void *base, int n, int np, long long rows) {
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// FP32 rows as make_map, box 4 x 128 without swizzle (the no-swizzle tail).
+bool make_tail_map(CUtensorMap &m, void *base, int n, int np, long long rows) {
+  auto fn = encode_fn();
+  if (fn == nullptr) return false;
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(n), static_cast<cuuint64_t>(rows)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(np) * 4};
+  cuuint32_t box[2] = {4u, static_cast<cuuint32_t>(kFib)};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 int ceil_to(int x, int m) { return (x + m - 1) / m * m; }
 
 }  // namespace
@@ -324,7 +354,7 @@ struct RotFd {
   float *lam_t = nullptr, *lam_s = nullptr;
   int *err = nullptr;
   struct Pass {
-    CUtensorMap map;
+    CUtensorMap map, tail;
     RotArgs args;
     size_t smem;
     int grid;
@@ -437,7 +467,15 @@ cudaError_t tc_fd_rot_create(RotFd *&out, std::vector<void *> &allocs, int d, co
     a.bytes_b = static_cast<uint32_t>(nkb[k]) * np_[k] * 128;
     a.off_stage = a.bytes_b;  // a multiple of 1024 (np is a multiple of 16)
     a.idesc = ptx::idesc_tf32(kFib, np_[k]);
-    const size_t stage_bytes = static_cast<size_t>(nkb[k]) * kBoxBytes;
+    // K groups: whole 32-value SW128 boxes and a tail of r <= 16 values in
+    // 4-value boxes (2 per K step of 8; the TMA unit zero-fills past n_k).  The
+    // stage size is a multiple of 1024 (an even number of 2048-byte tail boxes),
+    // so every stage's SW128 atoms stay 1024-aligned.
+    const int r = n[k] % kBoxK;
+    a.full_atoms = (r > 0 && r <= kTailMax) ? n[k] / kBoxK : nkb[k];
+    a.tail_boxes = (r > 0 && r <= kTailMax) ? 2 * ((r + 7) / 8) : 0;
+    a.stage_bytes = static_cast<uint32_t>(a.full_atoms) * kBoxBytes + static_cast<uint32_t>(a.tail_boxes) * kTailBoxBytes;
+    const size_t stage_bytes = a.stage_bytes;
     const size_t room = kSmemLimit - kStaticSmem - 1024 - a.bytes_b;
     a.stages = static_cast<int>(std::min<size_t>(kMaxStages, room / stage_bytes));
     if (a.stages < 2) {
@@ -446,7 +484,7 @@ cudaError_t tc_fd_rot_create(RotFd *&out, std::vector<void *> &allocs, int d, co
     }
     ps.smem = 1024 + a.bytes_b + a.stages * stage_bytes;
     float *in = f->inter[(st + 1) % 2];
-    if (!make_map(ps.map, in, n[k], npad[k], a.rows)) {
+    if (!make_map(ps.map, in, n[k], npad[k], a.rows) || !make_tail_map(ps.tail, in, n[k], npad[k], a.rows)) {
       err = "TF32 preconditioner: cuTensorMapEncodeTiled failed";
       return cudaErrorInvalidConfiguration;
     }
@@ -522,11 +560,11 @@ cudaError_t launch_passes(RotFd *f, IO *z, cudaStream_t s) {
     cfg.numAttrs = 1;
     cudaError_t e;
     if (ps.last)
-      e = cudaLaunchKernelEx(&cfg, rot_kernel<IO, false>, ps.map, a);
+      e = cudaLaunchKernelEx(&cfg, rot_kernel<IO, false>, ps.map, ps.tail, a);
     else if (ps.divide)
-      e = cudaLaunchKernelEx(&cfg, rot_kernel<float, true>, ps.map, a);
+      e = cudaLaunchKernelEx(&cfg, rot_kernel<float, true>, ps.map, ps.tail, a);
     else
-      e = cudaLaunchKernelEx(&cfg, rot_kernel<float, false>, ps.map, a);
+      e = cudaLaunchKernelEx(&cfg, rot_kernel<float, false>, ps.map, ps.tail, a);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
