@@ -103,6 +103,23 @@ typedef struct {
   int fp64_residuals; /* refine = 1 only.  0: provisional double-float outer
                        residuals as described under refine; 1: every outer
                        residual F - A u in FP64 */
+  /* Parametrization of the spatial domain (Sec. 4.4).  0: the unit cube with
+     the identity map.  1: the unit cube parametrized by the separable map
+     G(eta)_k = g_k(eta_k) = eta_k + geo_a[k] sin(2 pi eta_k) / (2 pi), a
+     non-uniformly stretched mesh of the same domain; the unknowns are the
+     coefficients of the mapped splines Bhat_i o G^{-1}, and A is the
+     least-squares matrix of Eq. a-form on the mapped basis (weighted 1D
+     factors; every 1D integral by 2p_s + 6 Gauss points per element).
+     geometry = 1 needs precision = STLS_FP64 and offers stls_apply_A,
+     stls_apply_precond and stls_solve (no lifting calls). */
+  int geometry;
+  double geo_a[3];    /* geometry = 1: stretch amplitudes, |geo_a[k]| < 1 (first d entries) */
+  int geo_precond;    /* geometry = 1: preconditioner.  0: P^G = D^{1/2} Pbar^G D^{1/2}
+                         of Sec. 4.4 (coefficients of Eq. coefficients-c at the
+                         element barycentres, univariate factors by the
+                         separation-of-variables algorithm of App. A.3 with two
+                         sweeps, D = diag(A) / diag(Pbar^G)); 1: Pbar^G alone;
+                         2: P of the parametric cube (the geometry ignored) */
 } stls_params;
 
 typedef struct {
@@ -217,8 +234,15 @@ enum stls_factor {
   STLS_F_EIGVEC = 3,    /* n x n  U of the preconditioner pencil, row-major */
   STLS_F_EIGVAL = 4,    /* n      Lambda of the preconditioner pencil, ascending */
   STLS_F_END = 5,       /* n      time basis at t = T (time only) */
-  STLS_F_INTEGRAL = 6   /* n      integrals of the reduced basis functions */
+  STLS_F_INTEGRAL = 6,  /* n      integrals of the reduced basis functions */
+  /* geometry = 1, space directions: the weighted factors of A (g = g_k) */
+  STLS_F_GEO_MASS = 7,  /* n x n  int b_i b_j g' */
+  STLS_F_GEO_STIFF = 8, /* n x n  int b'_i b'_j / g' */
+  STLS_F_GEO_BILAP = 9, /* n x n  int (L b_i)(L b_j) g',  L b = (1/g') (b' / g')' */
+  STLS_F_GEO_E = 10     /* n x n  int (L b_i) b_j g'  (not symmetric) */
 };
+/* With geometry = 1, STLS_F_EIGVEC / STLS_F_EIGVAL are those of the pencils of
+ * the context's preconditioner (Pbar^G unless geo_precond = 2). */
 
 /* Copy a 1D factor of direction `dir` (0..d-1 space, d = time) to host
  * memory.  Matrices are row-major. */

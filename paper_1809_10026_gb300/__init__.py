@@ -58,14 +58,18 @@ class Solver:
     mode products with FP32 accumulation; FP32 division by the eigenvalue
     sums; with refine=False every CG vector, A x and inner product in FP64).
     refine=True (mixed forms) solves by iterative refinement: FP64 residuals
-    F - A u and corrections, inner FP32 flexible CG.  Vectors are float64 CUDA tensors of
+    F - A u and corrections, inner FP32 flexible CG.
+    geo_a (FP64 only): stretch amplitudes a_k of the parametrization
+    g_k(s) = s + a_k sin(2 pi s) / (2 pi) of the cube (Sec. 4.4 setting);
+    geo_precond "PG" (P^G with the diagonal scaling), "Pbar" or "P" (the
+    parametric cube's P).  Vectors are float64 CUDA tensors of
     shape (batch, N) or (N,) for batch 1, in colexicographic order
     (direction 1 fastest, time slowest).
     """
 
     def __init__(self, d, p, n_el, T=1.0, precision="fp64", flexible=None, batch=1, p_t=None,
                  n_el_t=None, time_pencil="physical", device=None, refine=False, inner_tol=0.0,
-                 fp64_residuals=False):
+                 fp64_residuals=False, geo_a=None, geo_precond="PG"):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("stls.Solver needs a CUDA device (no CPU fallback)")
@@ -73,7 +77,7 @@ class Solver:
         self.device = torch.device("cuda" if device is None else device)
         self.lib = _lib.load()
         self.params = make_params(d, p, n_el, T, precision, flexible, batch, p_t, n_el_t, time_pencil,
-                                  refine, inner_tol, fp64_residuals)
+                                  refine, inner_tol, fp64_residuals, geo_a, geo_precond)
         self.ctx = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             stream = torch.cuda.current_stream(self.device).cuda_stream

@@ -9,7 +9,9 @@ STLS_OK, STLS_EINVAL, STLS_ENOMEM, STLS_ECUDA, STLS_ENOTCONV, STLS_EBREAKDOWN, S
 STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error",
                 4: "not converged", 5: "breakdown", 6: "non-finite value"}
 PRECISION = {"fp64": 0, "tf32": 1, "bf16": 2}
-FACTOR = {"mass": 0, "stiff": 1, "bilap": 2, "eigvec": 3, "eigval": 4, "end": 5, "integral": 6}
+FACTOR = {"mass": 0, "stiff": 1, "bilap": 2, "eigvec": 3, "eigval": 4, "end": 5, "integral": 6,
+          "geo_mass": 7, "geo_stiff": 8, "geo_bilap": 9, "geo_e": 10}
+GEO_PRECOND = {"PG": 0, "Pbar": 1, "P": 2}
 
 EXPORTS = ["stls_create", "stls_destroy", "stls_last_error", "stls_set_stream", "stls_sizes",
            "stls_apply_A", "stls_apply_A_df", "stls_apply_precond", "stls_solve", "stls_solve_host", "stls_apply_lift",
@@ -22,7 +24,8 @@ class Params(ctypes.Structure):
                 ("n_el_s", ctypes.c_int * 3), ("n_el_t", ctypes.c_int), ("T", ctypes.c_double),
                 ("precision", ctypes.c_int), ("flexible", ctypes.c_int), ("batch", ctypes.c_int),
                 ("time_pencil", ctypes.c_int), ("refine", ctypes.c_int), ("inner_tol", ctypes.c_double),
-                ("fp64_residuals", ctypes.c_int)]
+                ("fp64_residuals", ctypes.c_int), ("geometry", ctypes.c_int), ("geo_a", ctypes.c_double * 3),
+                ("geo_precond", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -84,7 +87,8 @@ def load():
 
 
 def make_params(d, p, n_el, T=1.0, precision="fp64", flexible=None, batch=1, p_t=None, n_el_t=None,
-                time_pencil="physical", refine=False, inner_tol=0.0, fp64_residuals=False):
+                time_pencil="physical", refine=False, inner_tol=0.0, fp64_residuals=False, geo_a=None,
+                geo_precond="PG"):
     n_el_s = [int(n_el)] * d if isinstance(n_el, int) else [int(v) for v in n_el]
     if len(n_el_s) != d:
         raise ValueError("n_el must be an int or a list of d ints")
@@ -103,4 +107,8 @@ def make_params(d, p, n_el, T=1.0, precision="fp64", flexible=None, batch=1, p_t
     prm.refine = int(bool(refine))
     prm.inner_tol = float(inner_tol)
     prm.fp64_residuals = int(bool(fp64_residuals))
+    prm.geometry = 0 if geo_a is None else 1
+    for k in range(3):
+        prm.geo_a[k] = float(geo_a[k]) if geo_a is not None and k < len(geo_a) else 0.0
+    prm.geo_precond = GEO_PRECOND[geo_precond]
     return prm

@@ -9,7 +9,12 @@
 //    the first, Sec. 2.2),
 //  * the generalized eigendecompositions of Algorithm 1, step 1, by Cholesky
 //    reduction and the cyclic Jacobi method (Golub & Van Loan, Matrix
-//    Computations, Sec. 8.5 and 8.7).
+//    Computations, Sec. 8.5 and 8.7),
+//  * for the stretched parametrization of the cube (geometry = 1): the
+//    weighted 1D factors of the least-squares matrix on the mapped splines,
+//    and the geometry-aware preconditioner of Sec. 4.4 (coefficients at the
+//    element barycentres, separation of variables of App. A.3, 1D matrices
+//    with element-wise constant weights).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -38,6 +43,13 @@ std::string validate_params(const stls_params &prm) {
   if (prm.refine == 1 && prm.precision == STLS_FP64) return "refine = 1 needs a mixed precision form";
   if (!(prm.inner_tol >= 0.0) || !(prm.inner_tol < 1.0)) return "inner_tol must be in [0, 1)";
   if (prm.fp64_residuals != 0 && prm.fp64_residuals != 1) return "fp64_residuals must be 0 or 1";
+  if (prm.geometry != 0 && prm.geometry != 1) return "geometry must be 0 or 1";
+  if (prm.geometry == 1) {
+    if (prm.precision != STLS_FP64) return "geometry = 1 needs precision = STLS_FP64";
+    if (prm.geo_precond < 0 || prm.geo_precond > 2) return "geo_precond must be 0, 1 or 2";
+    for (int k = 0; k < prm.d; ++k)
+      if (!(std::fabs(prm.geo_a[k]) < 1.0)) return "geo_a[k] must satisfy |geo_a[k]| < 1";
+  }
   return "";
 }
 
@@ -289,6 +301,205 @@ bool generalized_eig(int n, const double *Jm, const double *Mm, Eig1D &out, std:
   return true;
 }
 
+// Derivatives of the stretch map g(s) = s + a sin(2 pi s) / (2 pi).
+static double geo_dg(double a, double s) { return 1.0 + a * std::cos(2.0 * M_PI * s); }
+static double geo_d2g(double a, double s) { return -2.0 * M_PI * a * std::sin(2.0 * M_PI * s); }
+
+// Weighted factors of one space direction of the mapped cube (reduced basis),
+// by 2p + 6 Gauss points per element (the weights are not polynomials).
+static GeoDir build_geo_direction(const Dir1D &D, double a) {
+  const int p = D.p, m = D.m, n = D.n;
+  std::vector<double> Mf(m * m, 0.0), Kf(m * m, 0.0), Jf(m * m, 0.0), Ef(m * m, 0.0);
+  std::vector<double> gx, gw;
+  gauss_legendre(2 * p + 6, gx, gw);
+  double v0[kMaxDeg + 1], v1[kMaxDeg + 1], v2[kMaxDeg + 1], lb[kMaxDeg + 1];
+  for (int sp = p; sp < m; ++sp) {
+    const double lo = D.knots[sp], hi = D.knots[sp + 1];
+    if (!(hi > lo)) continue;
+    for (size_t q = 0; q < gx.size(); ++q) {
+      const double x = 0.5 * (hi - lo) * gx[q] + 0.5 * (lo + hi);
+      const double w = 0.5 * (hi - lo) * gw[q];
+      const double g1 = geo_dg(a, x), g2 = geo_d2g(a, x);
+      eval_span(D.knots, p, sp, x, v0, v1, v2);
+      for (int r = 0; r <= p; ++r) lb[r] = v2[r] / (g1 * g1) - v1[r] * g2 / (g1 * g1 * g1);
+      for (int r = 0; r <= p; ++r) {
+        const int gi = sp - p + r;
+        for (int c = 0; c <= p; ++c) {
+          const int gj = sp - p + c;
+          Mf[gi * m + gj] += w * g1 * v0[r] * v0[c];
+          Kf[gi * m + gj] += w / g1 * v1[r] * v1[c];
+          Jf[gi * m + gj] += w * g1 * lb[r] * lb[c];
+          Ef[gi * m + gj] += w * g1 * lb[r] * v0[c];
+        }
+      }
+    }
+  }
+  GeoDir G;
+  auto reduce = [&](const std::vector<double> &F, std::vector<double> &out) {
+    out.assign(static_cast<size_t>(n) * n, 0.0);
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) out[i * n + j] = F[(1 + i) * m + 1 + j];  // space: drop first and last
+  };
+  reduce(Mf, G.M);
+  reduce(Kf, G.K);
+  reduce(Jf, G.J);
+  reduce(Ef, G.E);
+  return G;
+}
+
+// int w_e b^(ord)_i b^(ord)_j with a weight constant on each element e (p+1
+// Gauss points per element: exact), on the reduced basis of D.
+static std::vector<double> element_weighted(const Dir1D &D, const std::vector<double> &we, int ord) {
+  const int p = D.p, m = D.m, n = D.n;
+  const int first = 1;
+  std::vector<double> Af(m * m, 0.0);
+  std::vector<double> gx, gw;
+  gauss_legendre(p + 1, gx, gw);
+  double v[3][kMaxDeg + 1];
+  int e = 0;
+  for (int sp = p; sp < m; ++sp) {
+    const double lo = D.knots[sp], hi = D.knots[sp + 1];
+    if (!(hi > lo)) continue;
+    for (size_t q = 0; q < gx.size(); ++q) {
+      const double x = 0.5 * (hi - lo) * gx[q] + 0.5 * (lo + hi);
+      const double w = 0.5 * (hi - lo) * gw[q] * we[e];
+      eval_span(D.knots, p, sp, x, v[0], v[1], v[2]);
+      for (int r = 0; r <= p; ++r)
+        for (int c = 0; c <= p; ++c) Af[(sp - p + r) * m + sp - p + c] += w * v[ord][r] * v[ord][c];
+    }
+    ++e;
+  }
+  std::vector<double> out(static_cast<size_t>(n) * n, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) out[i * n + j] = Af[(first + i) * m + first + j];
+  return out;
+}
+
+// App. A.3 in product form.  The omega-update sets omega^(k)_j from the min and
+// max over the slice i_k = j of C^(k) / prod_{l != k} mu^(l); the mu-update
+// sets mu^(k)_j from the min over the slice of the element-wise minimum, and
+// the max of the maximum, over coefficients l != k of C^(l) divided by its
+// product approximation and multiplied by mu^(k) (the estimate of mu^(k) that
+// c_l gives).  With C^(k) = prod_l F[k][l](i_l), every such min or max over a
+// slice is a product of the per-direction minima or maxima.
+void separate_product_form(const std::vector<std::vector<std::vector<double>>> &F, int maxit,
+                           std::vector<std::vector<double>> &mu, std::vector<std::vector<double>> &omega) {
+  const int D = static_cast<int>(F.size());
+  mu.assign(D, {});
+  omega.assign(D, {});
+  for (int l = 0; l < D; ++l) {
+    mu[l].assign(F[0][l].size(), 1.0);
+    omega[l].assign(F[0][l].size(), 1.0);
+  }
+  auto minmax_ratio = [](const std::vector<double> &f, const std::vector<double> &g, double &mn, double &mx) {
+    mn = f[0] / g[0];
+    mx = mn;
+    for (size_t i = 1; i < f.size(); ++i) {
+      const double r = f[i] / g[i];
+      mn = std::min(mn, r);
+      mx = std::max(mx, r);
+    }
+  };
+  for (int it = 0; it < maxit; ++it) {
+    for (int k = 0; k < D; ++k) {
+      double pmin = 1.0, pmax = 1.0;
+      for (int l = 0; l < D; ++l) {
+        if (l == k) continue;
+        double mn, mx;
+        minmax_ratio(F[k][l], mu[l], mn, mx);
+        pmin *= mn;
+        pmax *= mx;
+      }
+      for (size_t j = 0; j < omega[k].size(); ++j) omega[k][j] = F[k][k][j] * std::sqrt(pmin * pmax);
+    }
+    for (int k = 0; k < D; ++k) {
+      std::vector<double> ymin(mu[k].size(), 0.0), zmax(mu[k].size(), 0.0);
+      bool first = true;
+      for (int l = 0; l < D; ++l) {
+        if (l == k) continue;
+        // C^(l) / approx_l * mu^(k): direction l carries F[l][l] / omega^(l),
+        // direction k carries F[l][k], every other m carries F[l][m] / mu^(m)
+        double pmin, pmax;
+        minmax_ratio(F[l][l], omega[l], pmin, pmax);
+        for (int m = 0; m < D; ++m) {
+          if (m == k || m == l) continue;
+          double mn, mx;
+          minmax_ratio(F[l][m], mu[m], mn, mx);
+          pmin *= mn;
+          pmax *= mx;
+        }
+        for (size_t j = 0; j < mu[k].size(); ++j) {
+          const double lo = F[l][k][j] * pmin, hi = F[l][k][j] * pmax;
+          ymin[j] = first ? lo : std::min(ymin[j], lo);
+          zmax[j] = first ? hi : std::max(zmax[j], hi);
+        }
+        first = false;
+      }
+      for (size_t j = 0; j < mu[k].size(); ++j) mu[k][j] = std::sqrt(ymin[j] * zmax[j]);
+    }
+  }
+}
+
+// The 1D matrices of Pbar^G for the stretch map: coefficients of Eq.
+// coefficients-c at the element barycentres, c_k = ||J^-1 e_k||^4 |det J| T
+// = T g_k'^-3 prod_{l != k} g_l' and c_{d+1} = prod_l g_l' / T (per-direction
+// factors, the time factor constant), separated by two sweeps of App. A.3.
+static void build_geo_preconditioner(const stls_params &prm, HostSetup &hs) {
+  const int d = prm.d, D = d + 1;
+  std::vector<std::vector<double>> gp(d);
+  for (int k = 0; k < d; ++k) {
+    const int ne = prm.n_el_s[k];
+    gp[k].resize(ne);
+    for (int e = 0; e < ne; ++e) gp[k][e] = geo_dg(prm.geo_a[k], (e + 0.5) / ne);
+  }
+  std::vector<std::vector<std::vector<double>>> F(D, std::vector<std::vector<double>>(D));
+  for (int k = 0; k < D; ++k)
+    for (int l = 0; l < D; ++l) {
+      if (l == d) {  // time direction: constant factor
+        F[k][l].assign(prm.n_el_t, k < d ? prm.T : 1.0 / prm.T);
+        continue;
+      }
+      F[k][l] = gp[l];
+      if (k == l)
+        for (double &v : F[k][l]) v = 1.0 / (v * v * v);
+    }
+  std::vector<std::vector<double>> mu, om;
+  separate_product_form(F, 2, mu, om);
+  hs.pg_M.assign(d, {});
+  hs.pg_J.assign(d, {});
+  for (int k = 0; k < d; ++k) {
+    hs.pg_M[k] = element_weighted(hs.space[k], mu[k], 0);
+    hs.pg_J[k] = element_weighted(hs.space[k], om[k], 2);
+  }
+  const Dir1D th = build_direction(prm.n_el_t, prm.p_t, true, 1.0);  // parametric time
+  // the time direction's reduced basis drops only its first function
+  auto time_weighted = [&](const std::vector<double> &we, int ord) {
+    const int p = th.p, m = th.m, n = th.n;
+    std::vector<double> Af(m * m, 0.0), gx, gw;
+    gauss_legendre(p + 1, gx, gw);
+    double v[3][kMaxDeg + 1];
+    int e = 0;
+    for (int sp = p; sp < m; ++sp) {
+      const double lo = th.knots[sp], hi = th.knots[sp + 1];
+      if (!(hi > lo)) continue;
+      for (size_t q = 0; q < gx.size(); ++q) {
+        const double x = 0.5 * (hi - lo) * gx[q] + 0.5 * (lo + hi);
+        const double w = 0.5 * (hi - lo) * gw[q] * we[e];
+        eval_span(th.knots, p, sp, x, v[0], v[1], v[2]);
+        for (int r = 0; r <= p; ++r)
+          for (int c = 0; c <= p; ++c) Af[(sp - p + r) * m + sp - p + c] += w * v[ord][r] * v[ord][c];
+      }
+      ++e;
+    }
+    std::vector<double> out(static_cast<size_t>(n) * n, 0.0);
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) out[i * n + j] = Af[(1 + i) * m + 1 + j];
+    return out;
+  };
+  hs.pg_Mt = time_weighted(mu[d], 0);
+  hs.pg_Kt = time_weighted(om[d], 1);
+}
+
 bool build_setup(const stls_params &prm, HostSetup &hs, std::string &err) {
   err = validate_params(prm);
   if (!err.empty()) return false;
@@ -306,6 +517,19 @@ bool build_setup(const stls_params &prm, HostSetup &hs, std::string &err) {
   hs.time_pencil = prm.time_pencil == 0 ? hs.time : build_direction(prm.n_el_t, prm.p_t, true, 1.0);
   const Dir1D &Tp = hs.time_pencil;
   if (!generalized_eig(Tp.n, Tp.K.data(), Tp.M.data(), hs.eig_t, err)) return false;
+  hs.geo.clear();
+  if (prm.geometry == 1) {
+    for (int k = 0; k < prm.d; ++k) hs.geo.push_back(build_geo_direction(hs.space[k], prm.geo_a[k]));
+    if (prm.geo_precond != 2) {
+      // the preconditioner's pencils are those of Pbar^G
+      build_geo_preconditioner(prm, hs);
+      for (int k = 0; k < prm.d; ++k) {
+        const int n = hs.space[k].n;
+        if (!generalized_eig(n, hs.pg_J[k].data(), hs.pg_M[k].data(), hs.eig_s[k], err)) return false;
+      }
+      if (!generalized_eig(hs.time.n, hs.pg_Kt.data(), hs.pg_Mt.data(), hs.eig_t, err)) return false;
+    }
+  }
   return true;
 }
 
@@ -344,6 +568,15 @@ static int copy_factor(const stls::HostSetup &hs, int which, int dir, double *ou
       src = &D.end_values;
       break;
     case STLS_F_INTEGRAL: src = &D.integrals; break;
+    case STLS_F_GEO_MASS:
+    case STLS_F_GEO_STIFF:
+    case STLS_F_GEO_BILAP:
+    case STLS_F_GEO_E: {
+      if (is_time || hs.prm.geometry != 1) return STLS_EINVAL;
+      const stls::GeoDir &G = hs.geo[dir];
+      src = which == STLS_F_GEO_MASS ? &G.M : which == STLS_F_GEO_STIFF ? &G.K : which == STLS_F_GEO_BILAP ? &G.J : &G.E;
+      break;
+    }
     default: return STLS_EINVAL;
   }
   std::memcpy(out, src->data(), src->size() * sizeof(double));

@@ -2,7 +2,7 @@
 // FP64 (the solver's residuals) or FP32 (the inner solves of the refinement
 // form).
 //
-// One launch applies up to 8 terms out[t.out] += t.scale * (t.band x_k in[t.in])
+// One launch applies up to 12 terms out[t.out] += t.scale * (t.band x_k in[t.in])
 // along one mode, where every band is a 1D Galerkin matrix of half-width p
 // (Sec. 4.5: bands of width 2p+1).  One CTA owns 32 fibers of the mode-k
 // unfolding; each input tile is staged in shared memory with p zero rows

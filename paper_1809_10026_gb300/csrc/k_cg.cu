@@ -668,6 +668,17 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSM)
   }
 }
 
+// y[b, i] = x[b, i] w[i] (the diagonal scaling of the geometry-aware preconditioner)
+__global__ void __launch_bounds__(kThreads, kBlocksPerSM)
+    scale_kernel(const double *x, const double *__restrict__ w, double *y, long long N) {
+  const int b = blockIdx.y;
+  const double *xb = x + static_cast<size_t>(b) * N;
+  double *yb = y + static_cast<size_t>(b) * N;
+  for (long long i = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x; i < N;
+       i += static_cast<long long>(gridDim.x) * kThreads)
+    yb[i] = xb[i] * w[i];
+}
+
 __global__ void lift_combine_kernel(const double *__restrict__ Ls, const double *__restrict__ Js,
                                     const double *__restrict__ e, const double *__restrict__ m,
                                     double *__restrict__ y, long long Ns, int nt) {
@@ -820,6 +831,11 @@ cudaError_t launch_lift_reduce(const double *lam, const double *g, const double 
                                double *a, double *bsum, double *gsum, long long Ns, int nt, int B,
                                cudaStream_t s) {
   lift_reduce_kernel<<<dim3(grid_1d(Ns), B), kThreads, 0, s>>>(lam, g, e, m, a, bsum, gsum, Ns, nt);
+  return cudaGetLastError();
+}
+cudaError_t launch_scale(const double *x, const double *w, double *y, long long N, int B, cudaStream_t s) {
+  if (N < 0 || B < 1 || B > 65535) return cudaErrorInvalidValue;
+  if (N > 0) scale_kernel<<<dim3(grid_1d(N), B), kThreads, 0, s>>>(x, w, y, N);
   return cudaGetLastError();
 }
 cudaError_t launch_axpy(const double *x, const double *y, double alpha, double *out, long long n,

@@ -115,7 +115,7 @@ cudaError_t launch_modeprod_f64(const double *in, double *out, const double *W, 
                                 const double *lam_row, const double *lam_col, cudaStream_t s);
 
 // ---- banded multi-term mode product (A x, Eq. A_kron), T = double or float --------
-constexpr int kMaxBandIn = 4, kMaxBandOut = 4, kMaxBandTerms = 8;
+constexpr int kMaxBandIn = 4, kMaxBandOut = 4, kMaxBandTerms = 12;
 template <typename T>
 struct BandTermT {
   const T *band;  // n x (2p+1) band storage of a 1D matrix
@@ -217,5 +217,7 @@ cudaError_t launch_lift_reduce(const double *lam, const double *g, const double 
 // out = x + alpha * y (elementwise, n entries)
 cudaError_t launch_axpy(const double *x, const double *y, double alpha, double *out, long long n,
                         cudaStream_t s);
+// y[b, i] = x[b, i] * w[i] for B vectors of N entries (x == y allowed)
+cudaError_t launch_scale(const double *x, const double *w, double *y, long long N, int B, cudaStream_t s);
 
 }  // namespace stls

@@ -29,6 +29,7 @@ using stls::ModeView;
 template <typename T>
 struct AOps {
   T *band_M[3] = {}, *band_K[3] = {}, *band_J[3] = {};
+  T *band_E[3] = {}, *band_Et[3] = {};  // geometry = 1: int (L b_i) b_j g' and its transpose
   T *band_Kt = nullptr, *band_Mt = nullptr;
   // the same bands with rows padded to whole 16-byte vectors, and 2 K (fused A x)
   T *pad_M[3] = {}, *pad_K[3] = {}, *pad_J[3] = {}, *pad_2K[3] = {};
@@ -62,6 +63,8 @@ struct stls_ctx {
   double *alpha_partials = nullptr;  // fused (p, A p) of the inner solves: B * alpha_blocks(N_s)
   unsigned *alpha_tickets = nullptr;
   double *dF = nullptr, *du = nullptr;
+  double *geo_dinv = nullptr;  // geometry = 1, geo_precond = 0: D^{-1/2} of P^G (N entries)
+  double *geo_tmp = nullptr;   // B x N: the scaled input of Pbar^G
   CGState *st = nullptr, *st_host = nullptr;
   stls::RedWork rw{};
   stls::TcFd tc{};
@@ -331,6 +334,105 @@ int spatial_tree(stls_ctx *c, AOps<T> &A, const T *X, long long outer_mult, T *M
   return STLS_OK;
 }
 
+bool is_geometry(const stls_ctx *c) { return c->hs.prm.geometry == 1; }
+
+// Spatial factors of the least-squares matrix on the mapped cube (geometry =
+// 1; weighted 1D factors M^w, K^w, J^w, E in the band arrays):
+//   M_s = (x) M^w,  J_s = sum_k J^w_k + sum_{k != l} E_k (dir. k) E_l^T (dir. l),
+//   L_s = sum_k K^w_k  (M^w in the other directions),
+// by the recurrence over modes of the partial products m (all M^w), j (one
+// J^w or a completed E / E^T pair), e (an E waiting for an E^T in a later
+// direction) and f (an E^T waiting for an E): at every mode
+//   m' = M m,  j' = M j + J m + E^T e + E f,  e' = M e + E m,  f' = M f + E^T m.
+// L_s is needed on the last time slice only, by its own two-state recurrence
+// (m, l' = M l + K m) on that slice.
+int geometry_spatial(stls_ctx *c, AOps<double> &A, const double *X, double *Ms, double *Js, double *Ls_last) {
+  const int d = c->d, p = c->hs.prm.p_s;
+  const long long om = static_cast<long long>(c->B) * c->n_t;
+  const double *cur[4] = {X, nullptr, nullptr, nullptr};  // m, j, e, f
+  for (int k = 0; k < d; ++k) {
+    const bool last = k == d - 1;
+    double **bank = A.abuf + (k % 2) * 4;
+    stls::BandSpecT<double> s{};
+    s.p = p;
+    int in[4] = {-1, -1, -1, -1};
+    for (int a = 0; a < 4; ++a)
+      if (cur[a] != nullptr) {
+        in[a] = s.n_in;
+        s.in[s.n_in++] = cur[a];
+      }
+    int out[4] = {-1, -1, -1, -1};
+    if (last) {
+      out[0] = s.n_out;
+      s.out[s.n_out++] = Ms;
+      out[1] = s.n_out;
+      s.out[s.n_out++] = Js;
+    } else {
+      for (int a = 0; a < 4; ++a) {
+        out[a] = s.n_out;
+        s.out[s.n_out++] = bank[a];
+      }
+    }
+    auto add = [&](const double *band, int from, int to) {
+      if (in[from] < 0 || out[to] < 0) return;
+      s.term[s.n_terms++] = {band, in[from], out[to], 1.0};
+    };
+    add(A.band_M[k], 0, 0);
+    add(A.band_M[k], 1, 1);
+    add(A.band_J[k], 0, 1);
+    add(A.band_Et[k], 2, 1);
+    add(A.band_E[k], 3, 1);
+    add(A.band_M[k], 2, 2);
+    add(A.band_E[k], 0, 2);
+    add(A.band_M[k], 3, 3);
+    add(A.band_Et[k], 0, 3);
+    STLS_LAUNCH(stls::launch_banded<double>(s, spatial_view(c, k, om), c->stream), "banded (geometry)");
+    if (!last)
+      for (int a = 0; a < 4; ++a) cur[a] = bank[a];
+  }
+  if (Ls_last != nullptr) {
+    // last time slice of every right-hand side: the first mode reads it from X
+    // (stride N), later modes B x N_s buffers
+    const double *lm = X + static_cast<long long>(c->n_t - 1) * c->Ns, *ll = nullptr;
+    for (int k = 0; k < d; ++k) {
+      const bool last = k == d - 1;
+      stls::BandSpecT<double> s{};
+      s.p = p;
+      s.in[s.n_in++] = lm;
+      if (ll) s.in[s.n_in++] = ll;
+      double *om_ = c->lift_tmp[(k % 2) * 2], *ol = last ? Ls_last : c->lift_tmp[(k % 2) * 2 + 1];
+      if (!last) s.out[s.n_out++] = om_;
+      const int o_l = s.n_out;
+      s.out[s.n_out++] = ol;
+      if (!last) s.term[s.n_terms++] = {A.band_M[k], 0, 0, 1.0};
+      s.term[s.n_terms++] = {A.band_K[k], 0, o_l, 1.0};
+      if (ll) s.term[s.n_terms++] = {A.band_M[k], 1, o_l, 1.0};
+      stls::ModeView v = spatial_view(c, k, 1);
+      v.outer *= c->B;  // spatial_view(.., 1) covers one slice; B slices here
+      v.in_outer_stride = v.out_outer_stride = static_cast<long long>(v.n) * v.inner;
+      if (k == 0) {
+        // inputs are slices of X: B right-hand sides N apart, outer index over (b, higher modes)
+        v.outer = c->Ns / (static_cast<long long>(v.n) * v.inner);
+        stls::ModeView vb = v;
+        for (int b = 0; b < c->B; ++b) {
+          stls::BandSpecT<double> sb = s;
+          sb.in[0] = lm + static_cast<long long>(b) * c->N;
+          for (int o = 0; o < sb.n_out; ++o) sb.out[o] = s.out[o] + static_cast<long long>(b) * c->Ns;
+          STLS_LAUNCH(stls::launch_banded<double>(sb, vb, c->stream), "banded (geometry, L_s)");
+        }
+      } else {
+        v.outer = static_cast<long long>(c->B) * (c->Ns / (static_cast<long long>(v.n) * v.inner));
+        STLS_LAUNCH(stls::launch_banded<double>(s, v, c->stream), "banded (geometry, L_s)");
+      }
+      if (!last) {
+        lm = om_;
+        ll = ol;
+      }
+    }
+  }
+  return STLS_OK;
+}
+
 template <typename T>
 stls::FusedA<T> fused_args(const stls_ctx *c, const AOps<T> &A) {
   stls::FusedA<T> f{};
@@ -391,6 +493,33 @@ int apply_A_f32_alpha(stls_ctx *c, const float *p, float *q) {
 
 template <typename T>
 int apply_A_impl(stls_ctx *c, AOps<T> &A, const T *x, T *y) {
+  if constexpr (std::is_same_v<T, double>) {
+    if (is_geometry(c)) {
+      const int bank = (c->d - 1) % 2;
+      T *Ms = A.abuf[bank * 4 + 0], *Js = A.abuf[bank * 4 + 1];
+      int rc = geometry_spatial(c, A, x, Ms, Js, A.ls_buf);
+      if (rc) return rc;
+      stls::BandSpecT<T> s{};
+      s.p = c->hs.prm.p_t;
+      s.in[0] = Ms;
+      s.in[1] = Js;
+      s.n_in = 2;
+      s.out[0] = y;
+      s.n_out = 1;
+      s.term[0] = {A.band_Kt, 0, 0, T(1)};
+      s.term[1] = {A.band_Mt, 1, 0, T(1)};
+      s.n_terms = 2;
+      s.last_add = A.ls_buf;
+      s.last_out = 0;
+      ModeView v{};
+      v.n = c->n_t;
+      v.inner = c->Ns;
+      v.outer = c->B;
+      v.in_outer_stride = v.out_outer_stride = c->N;
+      STLS_LAUNCH(stls::launch_banded<T>(s, v, c->stream), "banded(time)");
+      return STLS_OK;
+    }
+  }
   if (stls::fused_A_supported(c->d, c->hs.prm.p_s, c->hs.prm.p_t)) {
     const stls::FusedA<T> f = fused_args(c, A);
     c->launches += c->d - 1;  // d launches in all
@@ -444,6 +573,10 @@ int fd_apply_impl(stls_ctx *c, const double *r, double *z) {
   }
   const int nprod = 2 * (c->d + 1);
   const double *src = r;
+  if (c->geo_dinv != nullptr) {  // P^G = D^{1/2} Pbar^G D^{1/2}: (P^G)^{-1} r = D^{-1/2} Pbar^{-1} D^{-1/2} r
+    STLS_LAUNCH(stls::launch_scale(r, c->geo_dinv, c->geo_tmp, c->N, c->B, c->stream), "scale");
+    src = c->geo_tmp;
+  }
   for (int s = 0; s < nprod; ++s) {
     const bool fwd = s <= c->d;
     const int k = fwd ? s : s - c->d - 1;
@@ -455,6 +588,8 @@ int fd_apply_impl(stls_ctx *c, const double *r, double *z) {
                 "modeprod");
     src = dst;
   }
+  if (c->geo_dinv != nullptr)
+    STLS_LAUNCH(stls::launch_scale(z, c->geo_dinv, z, c->N, c->B, c->stream), "scale");
   return STLS_OK;
 }
 
@@ -471,6 +606,72 @@ std::vector<double> spatial_eigenvalue_sums(const stls_ctx *c) {
     ls[idx] = s;
   }
   return ls;
+}
+
+// D^{-1/2} of P^G = D^{1/2} Pbar^G D^{1/2}, D = diag(A) / diag(Pbar^G) over the
+// colexicographic index (Sec. 4.4), from the diagonals of the 1D factors:
+//   diag(A) = Kt x Mw_s + Mt x (sum_k Jw_k + sum_{k != l} E_k E_l) + Wt x sum_k Kw_k,
+//   diag(Pbar^G) = Kg_t x Mg_s + Mg_t x sum_k Jg_k   (M in the other directions).
+std::vector<double> geometry_scaling(const stls_ctx *c) {
+  const stls::HostSetup &hs = c->hs;
+  const int d = c->d, nt = c->n_t;
+  auto diag = [](const std::vector<double> &A, int n) {
+    std::vector<double> v(n);
+    for (int i = 0; i < n; ++i) v[i] = A[static_cast<size_t>(i) * n + i];
+    return v;
+  };
+  std::vector<std::vector<double>> dMw(d), dKw(d), dJw(d), dE(d), dMg(d), dJg(d);
+  for (int k = 0; k < d; ++k) {
+    const int n = c->n_s[k];
+    dMw[k] = diag(hs.geo[k].M, n);
+    dKw[k] = diag(hs.geo[k].K, n);
+    dJw[k] = diag(hs.geo[k].J, n);
+    dE[k] = diag(hs.geo[k].E, n);
+    dMg[k] = diag(hs.pg_M[k], n);
+    dJg[k] = diag(hs.pg_J[k], n);
+  }
+  const std::vector<double> dKt = diag(hs.time.K, nt), dMt = diag(hs.time.M, nt);
+  const std::vector<double> dKgt = diag(hs.pg_Kt, nt), dMgt = diag(hs.pg_Mt, nt);
+  std::vector<double> out(c->N);
+  std::vector<int> idx(d);
+  for (long long sidx = 0; sidx < c->Ns; ++sidx) {
+    long long rem = sidx;
+    for (int k = 0; k < d; ++k) {
+      idx[k] = static_cast<int>(rem % c->n_s[k]);
+      rem /= c->n_s[k];
+    }
+    double ms = 1.0, mg = 1.0;
+    for (int k = 0; k < d; ++k) {
+      ms *= dMw[k][idx[k]];
+      mg *= dMg[k][idx[k]];
+    }
+    double js = 0.0, ls = 0.0, jg = 0.0;
+    for (int k = 0; k < d; ++k) {
+      double tj = dJw[k][idx[k]], tl = dKw[k][idx[k]], tg = dJg[k][idx[k]];
+      for (int l = 0; l < d; ++l)
+        if (l != k) {
+          tj *= dMw[l][idx[l]];
+          tl *= dMw[l][idx[l]];
+          tg *= dMg[l][idx[l]];
+        }
+      js += tj;
+      ls += tl;
+      jg += tg;
+      for (int l = 0; l < d; ++l) {
+        if (l == k) continue;
+        double te = dE[k][idx[k]] * dE[l][idx[l]];
+        for (int m = 0; m < d; ++m)
+          if (m != k && m != l) te *= dMw[m][idx[m]];
+        js += te;
+      }
+    }
+    for (int t = 0; t < nt; ++t) {
+      const double a = dKt[t] * ms + dMt[t] * js + (t == nt - 1 ? hs.time.end_values[t] * hs.time.end_values[t] : 0.0) * ls;
+      const double pg = dKgt[t] * mg + dMgt[t] * jg;
+      out[static_cast<size_t>(t) * c->Ns + sidx] = 1.0 / std::sqrt(a / pg);
+    }
+  }
+  return out;
 }
 
 // Residual history: after every read of the solver state, entry `iters` of
@@ -849,10 +1050,19 @@ int stls_create(stls_ctx **out, const stls_params *prm, void *cuda_stream) {
   const bool df = refine && P.fp64_residuals == 0 && stls::fused_A_supported(c->d, P.p_s, P.p_t);
   c->have_df = df;
   auto to_f32 = [](const std::vector<double> &v) { return std::vector<float>(v.begin(), v.end()); };
+  const bool geo = P.geometry == 1;
   for (int k = 0; k < c->d && !rc; ++k) {
     const stls::Dir1D &D = c->hs.space[k];
-    const std::vector<double> bM = stls::to_band(D.M, D.n, D.p), bK = stls::to_band(D.K, D.n, D.p),
-                              bJ = stls::to_band(D.J, D.n, D.p);
+    // the mapped cube's A uses the weighted factors (E and E^T for the cross terms)
+    const std::vector<double> &mM = geo ? c->hs.geo[k].M : D.M, &mK = geo ? c->hs.geo[k].K : D.K,
+                              &mJ = geo ? c->hs.geo[k].J : D.J;
+    const std::vector<double> bM = stls::to_band(mM, D.n, D.p), bK = stls::to_band(mK, D.n, D.p),
+                              bJ = stls::to_band(mJ, D.n, D.p);
+    if (geo) {
+      rc = upload(c, &c->a64.band_E[k], stls::to_band(c->hs.geo[k].E, D.n, D.p));
+      if (!rc) rc = upload(c, &c->a64.band_Et[k], stls::to_band(transpose(c->hs.geo[k].E, D.n), D.n, D.p));
+      if (rc) break;
+    }
     rc = upload(c, &c->a64.band_M[k], bM);
     if (!rc) rc = upload(c, &c->a64.band_K[k], bK);
     if (!rc) rc = upload(c, &c->a64.band_J[k], bJ);
@@ -906,6 +1116,11 @@ int stls_create(stls_ctx **out, const stls_params *prm, void *cuda_stream) {
     if (!rc) rc = dev_alloc(c, &c->alpha_tickets, c->B);
   }
   for (int a = 0; a < 4 && !rc; ++a) rc = dev_alloc(c, &c->lift_tmp[a], BNs);
+  if (!rc && geo && P.geo_precond == 0) {
+    // D = diag(A) / diag(Pbar^G) from the 1D diagonals; the apply scales by D^{-1/2}
+    rc = dev_alloc(c, &c->geo_tmp, BN);
+    if (!rc) rc = upload(c, &c->geo_dinv, geometry_scaling(c));
+  }
   if (!rc) rc = dev_alloc(c, &c->st, c->B);
   c->rw.grid = stls::red_grid_for(c->N);
   if (!rc) rc = dev_alloc(c, &c->rw.partials, static_cast<size_t>(c->B) * c->rw.grid * 2);
@@ -1028,6 +1243,7 @@ int stls_round_bf16(const double *x, double *y, long long n, void *cuda_stream) 
 
 int stls_apply_lift(stls_ctx *c, const double *c0, double *y) {
   if (c == nullptr) return STLS_EINVAL;
+  if (is_geometry(c)) return set_err(c, STLS_EINVAL, "lifting calls need geometry = 0");
   if (check_ptr(c, c0, "c0") || check_ptr(c, y, "y")) return STLS_EINVAL;
   double *Js = c->lift_tmp[0], *Ls = c->lift_tmp[1];
   int rc = spatial_tree<double>(c, c->a64, c0, c->B, nullptr, Js, Ls, nullptr);
@@ -1039,6 +1255,7 @@ int stls_apply_lift(stls_ctx *c, const double *c0, double *y) {
 
 int stls_lifted_rhs(stls_ctx *c, const double *F, const double *c0, double *rhs) {
   if (c == nullptr) return STLS_EINVAL;
+  if (is_geometry(c)) return set_err(c, STLS_EINVAL, "lifting calls need geometry = 0");
   if (check_ptr(c, F, "F") || check_ptr(c, c0, "c0") || check_ptr(c, rhs, "rhs")) return STLS_EINVAL;
   if (rhs == F || rhs == c0) return set_err(c, STLS_EINVAL, "lifted_rhs: rhs must not overlap F or c0");
   double *Gc0 = c->fd_tmp[0];  // B x N workspace
@@ -1050,6 +1267,7 @@ int stls_lifted_rhs(stls_ctx *c, const double *F, const double *c0, double *rhs)
 
 int stls_lift_add(stls_ctx *c, const double *w, const double *c0, double *u) {
   if (c == nullptr) return STLS_EINVAL;
+  if (is_geometry(c)) return set_err(c, STLS_EINVAL, "lifting calls need geometry = 0");
   if (check_ptr(c, w, "w") || check_ptr(c, c0, "c0") || check_ptr(c, u, "u")) return STLS_EINVAL;
   if (u == w || u == c0) return set_err(c, STLS_EINVAL, "lift_add: u must not overlap w or c0");
   // 1_{n_t} x c0 (+ 0 x c0) into the B x N workspace, then u = w + it
@@ -1062,6 +1280,7 @@ int stls_lift_add(stls_ctx *c, const double *w, const double *c0, double *u) {
 
 int stls_lift_adjoint(stls_ctx *c, const double *g, const double *lam, double *dc0) {
   if (c == nullptr) return STLS_EINVAL;
+  if (is_geometry(c)) return set_err(c, STLS_EINVAL, "lifting calls need geometry = 0");
   if (check_ptr(c, g, "g") || check_ptr(c, lam, "lam") || check_ptr(c, dc0, "dc0")) return STLS_EINVAL;
   // G^T lam = L_s (sum_t e_t lam_t) + J_s (sum_t m_t lam_t)   (L_s, J_s symmetric)
   double *a = c->lift_tmp[0], *bs = c->lift_tmp[1], *gs = c->lift_tmp[2];

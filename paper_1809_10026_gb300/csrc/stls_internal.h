@@ -29,15 +29,31 @@ struct Eig1D {
   std::vector<double> U, lam;
 };
 
+// Weighted 1D factors of the least-squares matrix on the mapped cube
+// (geometry = 1; g = g_k of the stretch map, L b = (1/g') (b' / g')').
+struct GeoDir {
+  std::vector<double> M, K, J, E;  // int b b g', int b' b' / g', int (Lb)(Lb) g', int (L b_i) b_j g'
+};
+
 // Host-side description of a problem: directions, pencils, banded factors.
 struct HostSetup {
   stls_params prm{};
   std::vector<Dir1D> space;  // d entries
   Dir1D time;                // physical time matrices on [0, T]
   Dir1D time_pencil;         // time matrices used by P (physical or parametric)
-  std::vector<Eig1D> eig_s;  // d entries
+  std::vector<Eig1D> eig_s;  // d entries: pencils of the preconditioner
   Eig1D eig_t;
+  std::vector<GeoDir> geo;   // geometry = 1: d entries
+  // geometry = 1, geo_precond != 2: the 1D matrices of Pbar^G (Sec. 4.4)
+  std::vector<std::vector<double>> pg_M, pg_J;  // d entries
+  std::vector<double> pg_Mt, pg_Kt;
 };
+
+// Separation of variables (App. A.3) for coefficient tensors in product form:
+// C^(k)[i_1..i_D] = prod_l F[k][l][i_l] with positive factors.  Writes the
+// univariate factors mu[l], omega[l] (lengths of F[0][l]); maxit sweeps.
+void separate_product_form(const std::vector<std::vector<std::vector<double>>> &F, int maxit,
+                           std::vector<std::vector<double>> &mu, std::vector<std::vector<double>> &omega);
 
 // Returns "" on success or an error message.
 std::string validate_params(const stls_params &prm);

@@ -119,3 +119,37 @@ def test_hat_time_pencil(lib):
     lt_hat = stls.host_factor("eigval", 1, 1, 3, 8, T=2.5, time_pencil="hat")
     # (M_t, K_t) = (T M_hat, K_hat / T): eigenvalues scale by 1 / T^2
     np.testing.assert_allclose(lt_phys, lt_hat / 2.5 ** 2, rtol=1e-12)
+
+
+@pytest.mark.parametrize("d,p,n_el,a", [(1, 3, 4, [0.5]), (2, 2, 3, [0.6, -0.4]), (3, 3, 2, [0.3, 0.5, -0.4])])
+def test_geometry_host_factors_match_oracle(d, p, n_el, a):
+    """Stretched parametrization (geometry = 1): the library's weighted 1D
+    factors of A equal the oracle's (same Gauss rule), and the eigenvalues of
+    the geometry-aware preconditioner's pencils (separation of variables in
+    product form on the host) equal those of the oracle's full-tensor version."""
+    from oracle.geometry import MappedProblem
+    mp = MappedProblem(d, p, n_el, a)
+    for k in range(d):
+        for name, key in (("geo_mass", "M"), ("geo_stiff", "K"), ("geo_bilap", "J"), ("geo_e", "E")):
+            A = stls.host_factor(name, k, d, p, n_el, geo_a=a)
+            R = mp.weighted[k][key]
+            assert np.abs(A - R).max() <= 1e-13 * np.abs(R).max(), (k, name)
+    PG = mp.preconditioner()
+    for k in range(d + 1):
+        lam = stls.host_factor("eigval", k, d, p, n_el, geo_a=a)
+        ref = PG.lam[k] if k < d else PG.lam_t
+        assert np.abs(lam - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_geometry_parameters_are_validated():
+    lib = _lib.load()
+    out = np.zeros(256)
+    for kw, msg in ((dict(precision="tf32", geo_a=[0.5, 0.5]), b"STLS_FP64"),
+                    (dict(geo_a=[1.0, 0.5]), b"|geo_a[k]| < 1"),
+                    (dict(geo_a=[0.2, 0.5], geo_precond="PG"), None)):
+        prm = stls.make_params(2, 3, 4, **kw)
+        rc = lib.stls_host_factor(ctypes.byref(prm), 0, 0, out.ctypes.data_as(ctypes.c_void_p))
+        if msg is None:
+            assert rc == _lib.STLS_OK
+        else:
+            assert rc == _lib.STLS_EINVAL and msg in lib.stls_last_error(None)
