@@ -288,6 +288,61 @@ int stls_phase_times(stls_ctx *ctx, double *ms_out4, long long *count_out4);
  * residuals, with the split of u).  ms_out, count_out: n entries or NULL. */
 int stls_phase_times_n(stls_ctx *ctx, int n, double *ms_out, long long *count_out);
 
+/* ---- local operations of a time-slab decomposition ----------------------------
+ * The paper leaves parallel solvers to future work (Sec. 1 and 6); these calls
+ * are the per-rank parts of a decomposition in which rank r owns the time
+ * slices [t0_r, t1_r) of every right-hand side (vectors of B x (t1-t0) x N_s
+ * entries, colexicographic within a slice).  A x (Eq. A_kron) is local in
+ * space and banded in time: each rank forms the spatial factors of its slices,
+ * exchanges p_t slices with each neighbour and applies the time band
+ * (stls_slab_spatial, stls_slab_time).  Algorithm 1 is local in space and
+ * dense in time: forward spatial products on the rank's slices, an
+ * all-to-all that hands rank r a range [s0_r, s1_r) of spatial indices for
+ * all times, the time products and the division on that range, the reverse
+ * all-to-all and the backward spatial products (stls_fd_spatial,
+ * stls_fd_time_chunk).  CG needs per-right-hand-side inner products, summed
+ * over ranks, and vector updates (stls_vec_dot, stls_vec_axpby).  The
+ * exchanges themselves belong to the caller (paper_1809_10026_gb300.timeslab).
+ * All calls are FP64, need geometry = 0, and run on the context's stream. */
+
+/* Spatial factors of Eq. A_kron on ns stacked spatial slices (any time slices
+ * of any right-hand sides, 1 <= ns <= B n_t): Ms = M_s x, Js = J_s x,
+ * Ls = L_s x per slice; any output may be NULL.  x, Ms, Js, Ls: device,
+ * ns x N_s. */
+int stls_slab_spatial(stls_ctx *ctx, const double *x, long long ns, double *Ms, double *Js, double *Ls);
+
+/* Time rows [t0, t1) of y = (K_t x M_s + M_t x J_s + W_t x L_s) x from the
+ * spatial factors of the slices [e0, e1) (the rank's rows and the halos):
+ * Ms_ext, Js_ext: device, B x (e1-e0) x N_s; requires
+ * 0 <= e0 <= t0 < t1 <= e1 <= n_t, e0 <= max(0, t0 - p_t) and
+ * e1 >= min(n_t, t1 + p_t).  Ls_last: device, B x N_s, L_s x of the last time
+ * slice, used (and then required) when t1 = n_t.  y: device,
+ * B x (t1-t0) x N_s. */
+int stls_slab_time(stls_ctx *ctx, const double *Ms_ext, const double *Js_ext, int e0, int e1, int t0, int t1,
+                   const double *Ls_last, double *y);
+
+/* Spatial mode products of Algorithm 1 on ns stacked spatial slices:
+ * forward != 0: y = (U_d^T x ... x U_1^T) x (step 2 without the time mode);
+ * forward == 0: y = (U_d x ... x U_1) x (step 4 without it).
+ * x, y: device, ns x N_s, 1 <= ns <= B n_t, must not overlap. */
+int stls_fd_spatial(stls_ctx *ctx, const double *x, double *y, long long ns, int forward);
+
+/* The time part of Algorithm 1 on the spatial indices [s0, s1): y = U_t ((U_t^T x)
+ * / (lambda_t[m] + lambda_s[s])), lambda_s[s] = sum_k lambda_k[i_k(s)] (steps 2-4 in
+ * the time mode, with the division of step 3).  x, y: device, B x n_t x (s1-s0)
+ * (the chunk's spatial index fastest), must not overlap; 0 <= s0 < s1 <= N_s. */
+int stls_fd_time_chunk(stls_ctx *ctx, const double *x, double *y, long long s0, long long s1);
+
+/* Per-right-hand-side inner products out_host[b] = sum_i x[b n + i] y[b n + i]
+ * (b < B) in FP64, in a fixed order (deterministic); synchronizes the stream.
+ * x, y: device, B x n. */
+int stls_vec_dot(stls_ctx *ctx, const double *x, const double *y, long long n, double *out_host);
+
+/* y[b n + i] = a_host[b] x[b n + i] + b_host[b] y[b n + i]: device vectors of
+ * B x n, host arrays of B scalars. */
+int stls_vec_axpby(stls_ctx *ctx, const double *a_host, const double *x, const double *b_host, double *y,
+                   long long n);
+
 /* ---- allocation-free preconditioner apply ------------------------------------
  * The paper has no counterpart to this entry point.  It serves callers that
  * cannot allocate device memory when they need the preconditioner: real-time

@@ -16,7 +16,9 @@ GEO_PRECOND = {"PG": 0, "Pbar": 1, "P": 2}
 EXPORTS = ["stls_create", "stls_destroy", "stls_last_error", "stls_set_stream", "stls_sizes",
            "stls_apply_A", "stls_apply_A_df", "stls_apply_precond", "stls_solve", "stls_solve_host", "stls_apply_lift",
            "stls_lifted_rhs", "stls_lift_add", "stls_lift_adjoint", "stls_override_eigenvalues", "stls_residual_history", "stls_get_factor", "stls_host_factor", "stls_launch_count",
-           "stls_enable_timing", "stls_phase_times", "stls_phase_times_n", "stls_apply_precond_noalloc", "stls_round_bf16"]
+           "stls_enable_timing", "stls_phase_times", "stls_phase_times_n", "stls_apply_precond_noalloc", "stls_round_bf16",
+           "stls_slab_spatial", "stls_slab_time", "stls_fd_spatial", "stls_fd_time_chunk", "stls_vec_dot",
+           "stls_vec_axpby"]
 
 
 class Params(ctypes.Structure):
@@ -82,6 +84,13 @@ def load():
     lib.stls_apply_precond_noalloc.argtypes = [i, ctypes.POINTER(ctypes.c_int), i, ctypes.POINTER(vp),
                                                ctypes.POINTER(vp), vp, vp, vp]
     lib.stls_round_bf16.argtypes = [vp, vp, ctypes.c_longlong, vp]
+    ll = ctypes.c_longlong
+    lib.stls_slab_spatial.argtypes = [vp, vp, ll, vp, vp, vp]
+    lib.stls_slab_time.argtypes = [vp, vp, vp, i, i, i, i, vp, vp]
+    lib.stls_fd_spatial.argtypes = [vp, vp, vp, ll, i]
+    lib.stls_fd_time_chunk.argtypes = [vp, vp, vp, ll, ll]
+    lib.stls_vec_dot.argtypes = [vp, vp, vp, ll, vp]
+    lib.stls_vec_axpby.argtypes = [vp, vp, vp, vp, vp, ll]
     _lib = lib
     return lib
 

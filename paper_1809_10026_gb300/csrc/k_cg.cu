@@ -668,6 +668,41 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSM)
   }
 }
 
+// out[b] = (x_b, y_b), deterministic like the CG reductions
+__global__ void __launch_bounds__(kThreads, kBlocksPerSM)
+    vec_dot_kernel(const double *__restrict__ x, const double *__restrict__ y, long long n, double *out, RedWork rw) {
+  const int b = blockIdx.y;
+  const double *xb = x + static_cast<size_t>(b) * n, *yb = y + static_cast<size_t>(b) * n;
+  double v[1] = {0.0};
+  const long long i0 = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x;
+  const long long S = static_cast<long long>(gridDim.x) * kThreads;
+  for (long long i = i0; i < n; i += kU * S) {
+    double xv[kU], yv[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u)
+      if (i + u * S < n) {
+        xv[u] = xb[i + u * S];
+        yv[u] = yb[i + u * S];
+      }
+#pragma unroll
+    for (int u = 0; u < kU; ++u)
+      if (i + u * S < n) v[0] = fma(xv[u], yv[u], v[0]);
+  }
+  double tot[1];
+  if (grid_sum<1>(v, rw, b, tot) && threadIdx.x == 0) out[b] = tot[0];
+}
+
+__global__ void __launch_bounds__(kThreads, kBlocksPerSM)
+    vec_axpby_kernel(const double *__restrict__ ab, const double *x, double *y, long long n) {
+  const int b = blockIdx.y, B = gridDim.y;
+  const double a = ab[b], c = ab[B + b];
+  const double *xb = x + static_cast<size_t>(b) * n;
+  double *yb = y + static_cast<size_t>(b) * n;
+  for (long long i = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x; i < n;
+       i += static_cast<long long>(gridDim.x) * kThreads)
+    yb[i] = fma(a, xb[i], c * yb[i]);
+}
+
 // y[b, i] = x[b, i] w[i] (the diagonal scaling of the geometry-aware preconditioner)
 __global__ void __launch_bounds__(kThreads, kBlocksPerSM)
     scale_kernel(const double *x, const double *__restrict__ w, double *y, long long N) {
@@ -831,6 +866,17 @@ cudaError_t launch_lift_reduce(const double *lam, const double *g, const double 
                                double *a, double *bsum, double *gsum, long long Ns, int nt, int B,
                                cudaStream_t s) {
   lift_reduce_kernel<<<dim3(grid_1d(Ns), B), kThreads, 0, s>>>(lam, g, e, m, a, bsum, gsum, Ns, nt);
+  return cudaGetLastError();
+}
+cudaError_t launch_vec_dot(const double *x, const double *y, long long n, int B, double *out, RedWork rw,
+                           cudaStream_t s) {
+  if (n < 0 || B < 1 || B > 65535) return cudaErrorInvalidValue;
+  vec_dot_kernel<<<dim3(rw.grid, B), kThreads, 0, s>>>(x, y, n, out, rw);
+  return cudaGetLastError();
+}
+cudaError_t launch_vec_axpby(const double *ab, const double *x, double *y, long long n, int B, cudaStream_t s) {
+  if (n < 0 || B < 1 || B > 65535) return cudaErrorInvalidValue;
+  if (n > 0) vec_axpby_kernel<<<dim3(grid_1d(n), B), kThreads, 0, s>>>(ab, x, y, n);
   return cudaGetLastError();
 }
 cudaError_t launch_scale(const double *x, const double *w, double *y, long long N, int B, cudaStream_t s) {

@@ -217,6 +217,11 @@ cudaError_t launch_lift_reduce(const double *lam, const double *g, const double 
 // out = x + alpha * y (elementwise, n entries)
 cudaError_t launch_axpy(const double *x, const double *y, double alpha, double *out, long long n,
                         cudaStream_t s);
+// out[b] = sum_i x[b n + i] y[b n + i] (fixed order), B vectors of n entries
+cudaError_t launch_vec_dot(const double *x, const double *y, long long n, int B, double *out, RedWork rw,
+                           cudaStream_t s);
+// y[b n + i] = ab[b] x[b n + i] + ab[B + b] y[b n + i]  (ab: device, 2B scalars)
+cudaError_t launch_vec_axpby(const double *ab, const double *x, double *y, long long n, int B, cudaStream_t s);
 // y[b, i] = x[b, i] * w[i] for B vectors of N entries (x == y allowed)
 cudaError_t launch_scale(const double *x, const double *w, double *y, long long N, int B, cudaStream_t s);
 

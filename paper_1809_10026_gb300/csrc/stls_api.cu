@@ -63,6 +63,7 @@ struct stls_ctx {
   double *alpha_partials = nullptr;  // fused (p, A p) of the inner solves: B * alpha_blocks(N_s)
   unsigned *alpha_tickets = nullptr;
   double *dF = nullptr, *du = nullptr;
+  double *vec_ab = nullptr, *vec_out = nullptr;  // scalars of stls_vec_axpby (2B), results of stls_vec_dot (B)
   double *geo_dinv = nullptr;  // geometry = 1, geo_precond = 0: D^{-1/2} of P^G (N entries)
   double *geo_tmp = nullptr;   // B x N: the scaled input of Pbar^G
   CGState *st = nullptr, *st_host = nullptr;
@@ -1122,6 +1123,8 @@ int stls_create(stls_ctx **out, const stls_params *prm, void *cuda_stream) {
     if (!rc) rc = upload(c, &c->geo_dinv, geometry_scaling(c));
   }
   if (!rc) rc = dev_alloc(c, &c->st, c->B);
+  if (!rc) rc = dev_alloc(c, &c->vec_ab, 2 * static_cast<size_t>(c->B));
+  if (!rc) rc = dev_alloc(c, &c->vec_out, c->B);
   c->rw.grid = stls::red_grid_for(c->N);
   if (!rc) rc = dev_alloc(c, &c->rw.partials, static_cast<size_t>(c->B) * c->rw.grid * 2);
   if (!rc) rc = dev_alloc(c, &c->rw.tickets, c->B);
@@ -1296,6 +1299,124 @@ int stls_lift_adjoint(stls_ctx *c, const double *g, const double *lam, double *d
   const long long n = static_cast<long long>(c->B) * c->Ns;
   STLS_LAUNCH(stls::launch_axpy(gs, La, -1.0, dc0, n, c->stream), "axpy");
   STLS_LAUNCH(stls::launch_axpy(dc0, Jb, -1.0, dc0, n, c->stream), "axpy");
+  return STLS_OK;
+}
+
+// ---- local operations of a time-slab decomposition -------------------------------------
+static int slab_check(stls_ctx *c, const char *what) {
+  if (c->hs.prm.precision != STLS_FP64 || is_geometry(c))
+    return set_err(c, STLS_EINVAL, std::string(what) + ": FP64 contexts with geometry = 0 only");
+  return STLS_OK;
+}
+
+int stls_slab_spatial(stls_ctx *c, const double *x, long long ns, double *Ms, double *Js, double *Ls) {
+  if (c == nullptr) return STLS_EINVAL;
+  if (int rc = slab_check(c, "slab_spatial")) return rc;
+  if (check_ptr(c, x, "x")) return STLS_EINVAL;
+  if (ns < 1 || ns > static_cast<long long>(c->B) * c->n_t)
+    return set_err(c, STLS_EINVAL, "slab_spatial: ns must be in [1, B n_t]");
+  if (Ms == nullptr && Js == nullptr && Ls == nullptr) return STLS_OK;
+  return spatial_tree<double>(c, c->a64, x, ns, Ms, Js, Ls, nullptr);
+}
+
+int stls_slab_time(stls_ctx *c, const double *Ms_ext, const double *Js_ext, int e0, int e1, int t0, int t1,
+                   const double *Ls_last, double *y) {
+  if (c == nullptr) return STLS_EINVAL;
+  if (int rc = slab_check(c, "slab_time")) return rc;
+  if (check_ptr(c, Ms_ext, "Ms_ext") || check_ptr(c, Js_ext, "Js_ext") || check_ptr(c, y, "y")) return STLS_EINVAL;
+  const int pt = c->hs.prm.p_t, nt = c->n_t;
+  if (!(0 <= e0 && e0 <= t0 && t0 < t1 && t1 <= e1 && e1 <= nt) || e0 > std::max(0, t0 - pt) ||
+      e1 < std::min(nt, t1 + pt))
+    return set_err(c, STLS_EINVAL, "slab_time: need 0 <= e0 <= t0 < t1 <= e1 <= n_t and halos of p_t slices");
+  if (t1 == nt && check_ptr(c, Ls_last, "Ls_last")) return STLS_EINVAL;
+  const int ne = e1 - e0, w = 2 * pt + 1;
+  // the time band on the extended rows (global rows e0 .. e1-1); rows whose band
+  // reaches past the extension are wrong and not kept
+  double *work = c->fd_tmp[0];
+  stls::BandSpec s{};
+  s.p = pt;
+  s.in[0] = Ms_ext;
+  s.in[1] = Js_ext;
+  s.n_in = 2;
+  s.out[0] = work;
+  s.n_out = 1;
+  s.term[0] = {c->a64.band_Kt + static_cast<size_t>(e0) * w, 0, 0, 1.0};
+  s.term[1] = {c->a64.band_Mt + static_cast<size_t>(e0) * w, 1, 0, 1.0};
+  s.n_terms = 2;
+  if (t1 == nt) {  // W_t x L_s on the last time slice (the last extended row)
+    s.last_add = Ls_last;
+    s.last_out = 0;
+  }
+  ModeView v{};
+  v.n = ne;
+  v.inner = c->Ns;
+  v.outer = c->B;
+  v.in_outer_stride = v.out_outer_stride = static_cast<long long>(ne) * c->Ns;
+  STLS_LAUNCH(stls::launch_banded(s, v, c->stream), "banded(time slab)");
+  const size_t row = sizeof(double) * static_cast<size_t>(c->Ns);
+  STLS_CK(cudaMemcpy2DAsync(y, row * (t1 - t0), work + static_cast<size_t>(t0 - e0) * c->Ns, row * ne,
+                            row * (t1 - t0), c->B, cudaMemcpyDeviceToDevice, c->stream),
+          "slab_time copy");
+  return STLS_OK;
+}
+
+int stls_fd_spatial(stls_ctx *c, const double *x, double *y, long long ns, int forward) {
+  if (c == nullptr) return STLS_EINVAL;
+  if (int rc = slab_check(c, "fd_spatial")) return rc;
+  if (check_ptr(c, x, "x") || check_ptr(c, y, "y")) return STLS_EINVAL;
+  if (x == y) return set_err(c, STLS_EINVAL, "fd_spatial: x and y must not overlap");
+  if (ns < 1 || ns > static_cast<long long>(c->B) * c->n_t)
+    return set_err(c, STLS_EINVAL, "fd_spatial: ns must be in [1, B n_t]");
+  const double *src = x;
+  for (int k = 0; k < c->d; ++k) {
+    double *dst = k == c->d - 1 ? y : c->fd_tmp[k % 2];
+    STLS_LAUNCH(stls::launch_modeprod_f64(src, dst, forward ? c->Uf[k] : c->Ub[k], spatial_view(c, k, ns),
+                                          nullptr, nullptr, c->stream),
+                "modeprod (spatial)");
+    src = dst;
+  }
+  return STLS_OK;
+}
+
+int stls_fd_time_chunk(stls_ctx *c, const double *x, double *y, long long s0, long long s1) {
+  if (c == nullptr) return STLS_EINVAL;
+  if (int rc = slab_check(c, "fd_time_chunk")) return rc;
+  if (check_ptr(c, x, "x") || check_ptr(c, y, "y")) return STLS_EINVAL;
+  if (x == y) return set_err(c, STLS_EINVAL, "fd_time_chunk: x and y must not overlap");
+  if (!(0 <= s0 && s0 < s1 && s1 <= c->Ns)) return set_err(c, STLS_EINVAL, "fd_time_chunk: need 0 <= s0 < s1 <= N_s");
+  ModeView v{};
+  v.n = c->n_t;
+  v.inner = s1 - s0;
+  v.outer = c->B;
+  v.in_outer_stride = v.out_outer_stride = static_cast<long long>(c->n_t) * (s1 - s0);
+  const int d = c->d;
+  STLS_LAUNCH(stls::launch_modeprod_f64(x, c->fd_tmp[0], c->Uf[d], v, c->lam_t, c->lam_s + s0, c->stream),
+              "modeprod (time, divide)");
+  STLS_LAUNCH(stls::launch_modeprod_f64(c->fd_tmp[0], y, c->Ub[d], v, nullptr, nullptr, c->stream),
+              "modeprod (time)");
+  return STLS_OK;
+}
+
+int stls_vec_dot(stls_ctx *c, const double *x, const double *y, long long n, double *out_host) {
+  if (c == nullptr) return STLS_EINVAL;
+  if (check_ptr(c, x, "x") || check_ptr(c, y, "y") || out_host == nullptr || n < 0)
+    return set_err(c, STLS_EINVAL, "vec_dot: NULL or misaligned pointer, or n < 0");
+  STLS_LAUNCH(stls::launch_vec_dot(x, y, n, c->B, c->vec_out, c->rw, c->stream), "vec_dot");
+  STLS_CK(cudaMemcpyAsync(out_host, c->vec_out, sizeof(double) * c->B, cudaMemcpyDeviceToHost, c->stream),
+          "vec_dot copy");
+  STLS_CK(cudaStreamSynchronize(c->stream), "sync");
+  return STLS_OK;
+}
+
+int stls_vec_axpby(stls_ctx *c, const double *a_host, const double *x, const double *b_host, double *y,
+                   long long n) {
+  if (c == nullptr) return STLS_EINVAL;
+  if (check_ptr(c, x, "x") || check_ptr(c, y, "y") || a_host == nullptr || b_host == nullptr || n < 0)
+    return set_err(c, STLS_EINVAL, "vec_axpby: NULL or misaligned pointer, or n < 0");
+  const size_t bytes = sizeof(double) * c->B;
+  STLS_CK(cudaMemcpyAsync(c->vec_ab, a_host, bytes, cudaMemcpyHostToDevice, c->stream), "vec_axpby upload");
+  STLS_CK(cudaMemcpyAsync(c->vec_ab + c->B, b_host, bytes, cudaMemcpyHostToDevice, c->stream), "vec_axpby upload");
+  STLS_LAUNCH(stls::launch_vec_axpby(c->vec_ab, x, y, n, c->B, c->stream), "vec_axpby");
   return STLS_OK;
 }
 
