@@ -174,6 +174,13 @@ int stls_apply_A(stls_ctx *ctx, const double *x, double *y);
  * 1..6 (the fused A x). */
 int stls_apply_A_df(stls_ctx *ctx, const double *x, double *y);
 
+/* y = A x in FP32 arithmetic: the operator of the refinement form's inner
+ * flexible CG (Sec. 4.2 on the system of Eq. A_kron), with the bands rounded
+ * once to FP32 and every product and sum an FP32 operation (fused
+ * multiply-add, fixed order).  x, y: device, B x N FP32, must not overlap.
+ * Errors: STLS_EINVAL unless the context has refine = 1. */
+int stls_apply_A_f32(stls_ctx *ctx, const float *x, float *y);
+
 /* z = P^{-1} r for the batch by fast diagonalization (Eq. preconditioner,
  * Algorithm 1, steps 2-4) in the context's precision.  r, z: device, B x N;
  * r == z is allowed. */

@@ -134,6 +134,21 @@ class Solver:
         _check(self.lib.stls_apply_A_df(self.ctx, self._ptr(x), self._ptr(y)), self.ctx)
         return y
 
+    def apply_A_f32(self, x, out=None):
+        """A x in FP32 arithmetic, the operator of the refinement form's inner
+        solves; x and the result are float32 CUDA tensors; refinement contexts only."""
+        t = self.torch
+        if not isinstance(x, t.Tensor) or x.dtype != t.float32 or x.device.type != "cuda":
+            raise TypeError("x must be a float32 CUDA tensor")
+        if x.numel() != self.batch * self.N:
+            raise ValueError("x must have batch * %d = %d entries, got %d" % (self.N, self.batch * self.N, x.numel()))
+        x = x.contiguous()
+        y = t.empty((self.batch, self.N) if self.batch > 1 else (self.N,), dtype=t.float32,
+                    device=self.device) if out is None else out
+        self._stream()
+        _check(self.lib.stls_apply_A_f32(self.ctx, self._ptr(x), self._ptr(y)), self.ctx)
+        return y
+
     def apply_precond(self, r, out=None):
         r = self._vec(r, self.N, "r")
         z = self._out(r.shape, self.N) if out is None else out

@@ -14,7 +14,7 @@ FACTOR = {"mass": 0, "stiff": 1, "bilap": 2, "eigvec": 3, "eigval": 4, "end": 5,
 GEO_PRECOND = {"PG": 0, "Pbar": 1, "P": 2}
 
 EXPORTS = ["stls_create", "stls_destroy", "stls_last_error", "stls_set_stream", "stls_sizes",
-           "stls_apply_A", "stls_apply_A_df", "stls_apply_precond", "stls_solve", "stls_solve_host", "stls_apply_lift",
+           "stls_apply_A", "stls_apply_A_df", "stls_apply_A_f32", "stls_apply_precond", "stls_solve", "stls_solve_host", "stls_apply_lift",
            "stls_lifted_rhs", "stls_lift_add", "stls_lift_adjoint", "stls_override_eigenvalues", "stls_residual_history", "stls_get_factor", "stls_host_factor", "stls_launch_count",
            "stls_enable_timing", "stls_phase_times", "stls_phase_times_n", "stls_apply_precond_noalloc", "stls_round_bf16",
            "stls_slab_spatial", "stls_slab_time", "stls_fd_spatial", "stls_fd_time_chunk", "stls_vec_dot",
@@ -65,6 +65,7 @@ def load():
                                ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_int)]
     lib.stls_apply_A.argtypes = [vp, vp, vp]
     lib.stls_apply_A_df.argtypes = [vp, vp, vp]
+    lib.stls_apply_A_f32.argtypes = [vp, vp, vp]
     lib.stls_apply_precond.argtypes = [vp, vp, vp]
     lib.stls_solve.argtypes = [vp, vp, vp, ctypes.c_double, i, ctypes.POINTER(SolveInfo)]
     lib.stls_solve_host.argtypes = [vp, vp, vp, ctypes.c_double, i, ctypes.POINTER(SolveInfo)]

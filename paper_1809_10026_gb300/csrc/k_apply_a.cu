@@ -189,6 +189,7 @@ __device__ __forceinline__ void slice_body(const SliceArgs<T> &a) {
   const long long s = act ? col / n1 : 0;
   const int x = act ? static_cast<int>(col - s * n1) : 0;
   const long long own = act ? s * area + x : 0;
+  const long long own_o = act ? s * a.out_area + x : 0;  // in the (possibly padded) output slices
   unsigned valid = 0;  // bit w: neighbour i_1 = x - P + w lies in the slice
   if (MASK) {
 #pragma unroll
@@ -243,8 +244,8 @@ __device__ __forceinline__ void slice_body(const SliceArgs<T> &a) {
   for (int w = 0; w < W; ++w) wm[w] = wj[w] = wk[w] = T(0);
   const bool ls_row = a.ls_last != nullptr && act && (s % a.n_t) == a.n_t - 1;
   const bool need_k = a.ls_last == nullptr || ls_row;
-  T *om_p = a.out_m + own, *oj_p = a.out_j + own;
-  T *ok_p = a.ls_last == nullptr ? a.out_k + own
+  T *om_p = a.out_m + own_o, *oj_p = a.out_j + own_o;
+  T *ok_p = a.ls_last == nullptr ? a.out_k + own_o
                                  : (ls_row ? a.ls_last + (s / a.n_t) * area + x : nullptr);
   int slot = 0;  // ring slot of row yy; row yy + D goes to the slot before it
   // one row yy: direction 1 of row yy (from the staged row), then direction 2
@@ -553,6 +554,257 @@ __global__ void __launch_bounds__(kAThreads) tpass_kernel(const __grid_constant_
   }
 }
 
+// ---- direction 3 and time in one sweep (FP32) -----------------------------------------
+// A CTA owns 32 consecutive columns c = (i_1, i_2) (one warp per i_3 row, so
+// every access is a 128-byte row segment), Z consecutive rows i_3 and one
+// right-hand side; thread (i_3, c) walks t.  At each t the CTA stages the rows
+// i_3 = z0 - P .. z0 + Z + P - 1 of m, j', k in shared memory (16-byte
+// cp.async, D time slices ahead; rows outside the mesh are zero-filled): the
+// direction-1/2 kernel writes these three states with every (t, i_3) slice
+// padded to a multiple of 4 values, so that row segments are 16-byte aligned.
+// Each thread forms
+//   M_s x = M3 m,  J_s x = M3 j' + J3 m + 2 K3 k   (and L_s x = M3 k + K3 m on
+//   the last time slice)
+// from 2P+1 staged rows, keeps M_s x and J_s x in time windows of 2P+1 rows and
+// emits y = K_t (M_s x) + M_t (J_s x) (+ L_s x on the last slice) for the time
+// row P behind: 4 vector passes instead of the 8 of a direction-3 pass and a
+// time pass (5 with the fused (p, A p)).  Each sum of several band products is
+// formed as independent FMA chains, one per band, added at the end.  The band
+// rows shared by the interior rows of direction 3 and of time are kernel
+// parameters (constant bank); warps of a boundary row i_3 read theirs from
+// the band arrays, and time groups touching a boundary row or the last slice
+// take a checked path.
+constexpr int kZtCols = 32;
+constexpr int kZtDepth = 4;
+constexpr int kZtMaxZ = 12;
+constexpr int kZtChunks = 2;  // 16-byte chunks a thread stages per time slice (checked on the host)
+constexpr int kZtMaxW = 2 * kFusedMaxP + 1;
+
+struct ZTArgs {
+  const float *m, *j, *k;  // (b, t, i_3) slices of `pitch` values (n1 n2 rounded up to 4)
+  float *y;
+  AlphaFuse fuse;
+  const float *bM3, *bJ3, *bK3, *b2K3;  // padded direction-3 bands (row stride ws)
+  const float *bKt, *bMt;               // padded time bands (row stride wt)
+  float iKt[kZtMaxW], iMt[kZtMaxW];     // the time band rows [lo_t, hi_t) all equal these
+  float i3[4][kZtMaxW];                 // rows [lo3, hi3) of M3, J3, 2 K3, K3 all equal these
+  long long inner, pitch;               // n1 n2 and its rounding up to a multiple of 4
+  int n3, nt, Z, ws, wt, lo3, hi3, lo_t, hi_t;
+};
+
+// 16-byte asynchronous copy into shared memory (zero-filled when `valid` is
+// false: no global bytes are read then).
+__device__ __forceinline__ void cp_async16(float *smem, const float *gmem, bool valid) {
+  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(valid ? 16 : 0)
+               : "memory");
+}
+
+template <int W>
+__device__ __forceinline__ float chain_g(const float *__restrict__ c, const float (&v)[W]) {  // c in global memory
+  float acc = 0.f;
+#pragma unroll
+  for (int w = 0; w < W; ++w) acc = fmaf(__ldg(c + w), v[w], acc);
+  return acc;
+}
+
+template <int P, bool FUSE>
+__global__ void __launch_bounds__(kZtCols * kZtMaxZ, 2) zt_kernel(const __grid_constant__ ZTArgs a) {
+  constexpr int W = 2 * P + 1, D = kZtDepth, R = D + 1, KC = kZtChunks;
+  extern __shared__ __align__(16) float zt_smem[];
+  const int tx = threadIdx.x, ty = threadIdx.y, Z = a.Z, ZR = Z + 2 * P;
+  const int tid = ty * kZtCols + tx, nth = Z * kZtCols;
+  const int n3 = a.n3, nt = a.nt;
+  const long long inner = a.inner, slice = static_cast<long long>(n3) * inner;
+  const long long pslice = static_cast<long long>(n3) * a.pitch;
+  const long long c0 = static_cast<long long>(blockIdx.x) * kZtCols, cc = c0 + tx;
+  const int z0 = blockIdx.y * Z, i3 = z0 + ty;
+  const bool act = cc < inner && i3 < n3;
+  const bool bdry = i3 < n3 && (i3 < a.lo3 || i3 >= a.hi3);  // the same in the whole warp
+  const long long b = blockIdx.z;
+  // y and p of (b, t = 0, i_3, c) in the natural order
+  const long long obase = b * nt * slice + static_cast<long long>(i3 < n3 ? i3 : 0) * inner + (cc < inner ? cc : 0);
+  const int roff = (i3 < n3 ? i3 : 0) * a.ws;  // this row of the direction-3 bands
+  // this thread's 16-byte chunks of a staged slice: chunk e = tid + q nth of
+  // the 3 x ZR x 8 chunks (array, row, 4 columns)
+  // slot: m, j', k rows, then (FUSE) p of this CTA's (i_3, c) at time t - P
+  const int arr_floats = ZR * kZtCols, slot_floats = 3 * arr_floats + (FUSE ? Z * kZtCols : 0);
+  const float *gsrc[KC];
+  int sdst[KC];
+  unsigned vmask = 0, nk = 0;
+#pragma unroll
+  for (int q = 0; q < KC; ++q) {
+    const int e = tid + q * nth;
+    gsrc[q] = a.m;
+    sdst[q] = 0;
+    if (e < 3 * ZR * 8) {
+      nk = q + 1;
+      const int arr = e / (ZR * 8), rem = e - arr * (ZR * 8), row = rem >> 3, ch = rem & 7;
+      const int gi3 = z0 - P + row;
+      const long long col = c0 + 4 * ch;
+      const float *base = arr == 0 ? a.m : (arr == 1 ? a.j : a.k);
+      sdst[q] = arr * arr_floats + row * kZtCols + 4 * ch;
+      gsrc[q] = base + b * nt * pslice;
+      if (gi3 >= 0 && gi3 < n3 && col < a.pitch) {
+        gsrc[q] += static_cast<long long>(gi3) * a.pitch + col;
+        vmask |= 1u << q;
+      }
+    }
+  }
+  auto issue = [&](int t, int slot) {
+    if (t < nt) {
+      const long long toff = static_cast<long long>(t) * pslice;
+      float *dst = zt_smem + slot * slot_floats;
+#pragma unroll
+      for (int q = 0; q < KC; ++q)
+        if (q < static_cast<int>(nk)) cp_async16(dst + sdst[q], gsrc[q] + toff, (vmask >> q) & 1u);
+      if constexpr (FUSE)
+        if (t >= P) cp_async_elem(dst + 3 * arr_floats + tid, a.fuse.p + obase + static_cast<long long>(t - P) * slice, act);
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int e = 0; e < D; ++e) issue(e, e);
+  float wMs[W], wJs[W];
+#pragma unroll
+  for (int w = 0; w < W; ++w) wMs[w] = wJs[w] = 0.f;
+  float ls = 0.f;  // L_s x of the last time slice
+  Dot2f acc;
+  int slot = 0;
+  // time row tt: M_s x and J_s x from the staged rows into the windows, then
+  // y of time row tt - P.  FAST: tt < nt - 1 and row tt - P an interior time row.
+  auto step = [&](int tt, auto fast) {
+    constexpr bool FAST = decltype(fast)::value;
+    const int y = tt - P;
+    const bool emit = FAST || (y >= 0 && y < nt);
+    float pv = 0.f;  // p of the emitted row: staged with the slice, or loaded in the last P steps
+    if constexpr (FUSE)
+      if (!FAST && tt >= nt && emit && act) pv = a.fuse.p[obase + static_cast<long long>(y) * slice];
+    float ms = 0.f, js = 0.f;
+    if (FAST || tt < nt) {
+      cp_async_wait<D - 1>();
+      __syncthreads();
+      if constexpr (FUSE)
+        if (emit) pv = zt_smem[slot * slot_floats + 3 * arr_floats + tid];
+      const float *sm = zt_smem + slot * slot_floats + ty * kZtCols + tx;
+      float mv[W], jv[W], kv[W];
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        mv[w] = sm[w * kZtCols];
+        jv[w] = sm[arr_floats + w * kZtCols];
+        kv[w] = sm[2 * arr_floats + w * kZtCols];
+      }
+      if (!bdry) {
+        float j1 = 0.f, j2 = 0.f, j3 = 0.f;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+          ms = fmaf(a.i3[0][w], mv[w], ms);
+          j1 = fmaf(a.i3[0][w], jv[w], j1);
+          j2 = fmaf(a.i3[1][w], mv[w], j2);
+          j3 = fmaf(a.i3[2][w], kv[w], j3);
+        }
+        js = (j1 + j2) + j3;
+        if (!FAST && tt == nt - 1) {
+          float l1 = 0.f, l2 = 0.f;
+#pragma unroll
+          for (int w = 0; w < W; ++w) {
+            l1 = fmaf(a.i3[0][w], kv[w], l1);
+            l2 = fmaf(a.i3[3][w], mv[w], l2);
+          }
+          ls = l1 + l2;
+        }
+      } else {
+        ms = chain_g(a.bM3 + roff, mv);
+        js = (chain_g(a.bM3 + roff, jv) + chain_g(a.bJ3 + roff, mv)) + chain_g(a.b2K3 + roff, kv);
+        if (!FAST && tt == nt - 1) ls = chain_g(a.bM3 + roff, kv) + chain_g(a.bK3 + roff, mv);
+      }
+      issue(tt + D, slot == 0 ? R - 1 : slot - 1);
+      slot = slot == R - 1 ? 0 : slot + 1;
+    }
+    slide(wMs, ms);
+    slide(wJs, js);
+    if (emit) {
+      float o1 = 0.f, o2 = 0.f;
+      if (FAST || (y >= a.lo_t && y < a.hi_t)) {
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+          o1 = fmaf(a.iKt[w], wMs[w], o1);
+          o2 = fmaf(a.iMt[w], wJs[w], o2);
+        }
+      } else {
+        o1 = chain_g(a.bKt + static_cast<size_t>(y) * a.wt, wMs);
+        o2 = chain_g(a.bMt + static_cast<size_t>(y) * a.wt, wJs);
+      }
+      float out = o1 + o2;
+      if (!FAST && y == nt - 1) out += ls;
+      if (act) {
+        a.y[obase + static_cast<long long>(y) * slice] = out;
+        if constexpr (FUSE) acc.add(pv, out);
+      }
+    }
+  };
+  for (int t0 = 0; t0 < nt + P; t0 += W) {
+    if (t0 - P >= a.lo_t && t0 - P + W <= a.hi_t && t0 + W <= nt - 1) {
+#pragma unroll
+      for (int u = 0; u < W; ++u) step(t0 + u, std::true_type{});
+    } else {
+#pragma unroll
+      for (int u = 0; u < W; ++u)
+        if (t0 + u < nt + P) step(t0 + u, std::false_type{});
+    }
+  }
+  cp_async_wait<0>();
+  if constexpr (FUSE) {
+    // block sum in a fixed order, then the blocks of this right-hand side
+    __shared__ double sh[kZtMaxZ];
+    __shared__ bool is_last;
+    double v = acc.value();
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) v += __shfl_xor_sync(0xffffffffu, v, s);
+    if (tx == 0) sh[ty] = v;
+    __syncthreads();
+    const unsigned nb = gridDim.x * gridDim.y, bi = blockIdx.y * gridDim.x + blockIdx.x, o = blockIdx.z;
+    const AlphaFuse &fz = a.fuse;
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < Z; ++w) t += sh[w];
+      fz.partials[static_cast<size_t>(o) * nb + bi] = t;
+      __threadfence();
+      is_last = atomicAdd(fz.tickets + o, 1u) == nb - 1;
+    }
+    __syncthreads();
+    if (is_last) {
+      __threadfence();
+      const volatile double *src = fz.partials + static_cast<size_t>(o) * nb;
+      double t = 0.0;
+      for (unsigned g = tid; g < nb; g += nth) t += src[g];
+#pragma unroll
+      for (int s = 16; s > 0; s >>= 1) t += __shfl_xor_sync(0xffffffffu, t, s);
+      __syncthreads();
+      if (tx == 0) sh[ty] = t;
+      __syncthreads();
+      if (tid == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < Z; ++w) tot += sh[w];
+        fz.tickets[o] = 0u;
+        CGState &st = fz.st[o];
+        if (st.active) {
+          st.pq = tot;
+          if (!isfinite(tot)) {
+            st.status = STLS_ENONFINITE;
+            st.active = 0;
+          } else if (!(tot > 0.0)) {
+            st.status = STLS_EBREAKDOWN;
+            st.active = 0;
+          } else {
+            st.alpha = st.rz / tot;
+          }
+        }
+      }
+    }
+  }
+}
+
 // ---- double-float images of FP64 vectors ------------------------------------------------
 constexpr int kDfThreads = 256;
 
@@ -628,6 +880,55 @@ cudaError_t launch_tpass_p(const TArgs<T> &a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Rows of i_3 per CTA of the fused direction-3 and time kernel: n3 split into
+// ceil(n3 / 12) equal groups (65 -> 6 x 11); 0 when n3 < 8 (the two passes
+// are used then).
+int zt_rows(int n3, int p) {
+  if (n3 < 8) return 0;
+  const int groups = (n3 + kZtMaxZ - 1) / kZtMaxZ;
+  const int Z = (n3 + groups - 1) / groups;
+  // every thread stages at most kZtChunks 16-byte chunks of the 3 (Z + 2p) rows
+  return 3 * (Z + 2 * p) * 8 <= kZtChunks * kZtCols * Z ? Z : 0;
+}
+
+template <int P>
+cudaError_t launch_zt_p(const ZTArgs &a, int B, cudaStream_t s) {
+  const long long gx = (a.inner + kZtCols - 1) / kZtCols;
+  const int gy = (a.n3 + a.Z - 1) / a.Z;
+  if (gx > 0x7fffffffLL || B > 65535) return cudaErrorInvalidConfiguration;
+  const bool fuse = a.fuse.p != nullptr;
+  const size_t smem = static_cast<size_t>(kZtDepth + 1) * (3 * (a.Z + 2 * P) + (fuse ? a.Z : 0)) * kZtCols *
+                      sizeof(float);
+  static size_t raised[2] = {0, 0};  // dynamic shared memory already allowed, per variant
+  if (smem > 48 * 1024 && raised[fuse] < smem) {
+    cudaError_t e = fuse ? cudaFuncSetAttribute(zt_kernel<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                static_cast<int>(smem))
+                         : cudaFuncSetAttribute(zt_kernel<P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    raised[fuse] = smem;
+  }
+  if (gx > 0 && B > 0) {
+    const dim3 grid(static_cast<unsigned>(gx), static_cast<unsigned>(gy), static_cast<unsigned>(B));
+    const dim3 block(kZtCols, static_cast<unsigned>(a.Z));
+    if (fuse)
+      zt_kernel<P, true><<<grid, block, smem, s>>>(a);
+    else
+      zt_kernel<P, false><<<grid, block, smem, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t dispatch_zt(int p, const ZTArgs &a, int B, cudaStream_t s) {
+  switch (p) {
+    case 1: return launch_zt_p<1>(a, B, s);
+    case 2: return launch_zt_p<2>(a, B, s);
+    case 3: return launch_zt_p<3>(a, B, s);
+    case 4: return launch_zt_p<4>(a, B, s);
+    default: return cudaErrorInvalidValue;  // degrees 5, 6 take the two passes
+  }
+}
+
 template <typename T>
 cudaError_t dispatch_slice(int p, const SliceArgs<T> &a, cudaStream_t s) {
   switch (p) {
@@ -667,7 +968,10 @@ cudaError_t dispatch_tpass(int p, const TArgs<T> &a, cudaStream_t s) {
 
 }  // namespace
 
-int alpha_blocks(long long Ns) { return static_cast<int>(blocks_for(Ns)); }
+// Partial sums of the fused (p, A p): one per block of the last kernel of the
+// product, at most ceil(N_s / 128) (time pass) or ceil(n1 n2 / 32) ceil(n3 / Z)
+// <= N_s / 32 + 129 (fused direction-3 and time kernel, Z >= 8, n3 <= 128).
+int alpha_blocks(long long Ns) { return static_cast<int>(4 * blocks_for(Ns) + 129); }
 
 int band_row_stride(int p, int elem_bytes) {
   const int w = 2 * p + 1, l = 16 / elem_bytes;
@@ -697,6 +1001,13 @@ cudaError_t launch_fused_A(const FusedA<T> &f, const T *x, T *y, cudaStream_t s)
   sa.bK2 = f.bK[1];
   sa.b2K2 = f.b2K[1];
   sa.slices = static_cast<long long>(f.B) * f.n_t * n3;
+  // FP32, three spatial directions: direction 3 and time in one kernel, which
+  // reads m, j', k in slices padded to 16 bytes
+  int zt_Z = 0;
+  if constexpr (std::is_same<T, float>::value)
+    if (f.d == 3 && f.p_t == f.p_s && f.p_s <= 4) zt_Z = zt_rows(f.n[2], f.p_s);  // higher degrees: two passes
+  const long long pitch = zt_Z > 0 ? (n1 * n2 + 3) / 4 * 4 : n1 * n2;
+  sa.out_area = pitch;
   sa.n1 = f.n[0];
   sa.n2 = f.n[1];
   sa.n_t = f.n_t;
@@ -717,6 +1028,40 @@ cudaError_t launch_fused_A(const FusedA<T> &f, const T *x, T *y, cudaStream_t s)
   }
   cudaError_t e = dispatch_slice<T>(f.p_s, sa, s);
   if (e != cudaSuccess) return e;
+  if constexpr (std::is_same<T, float>::value) {
+    if (zt_Z > 0) {
+      ZTArgs za{};
+      za.m = f.work[0];
+      za.j = f.work[1];
+      za.k = f.work[2];
+      za.y = y;
+      za.fuse = f.fuse;
+      za.bM3 = f.bM[2];
+      za.bJ3 = f.bJ[2];
+      za.bK3 = f.bK[2];
+      za.b2K3 = f.b2K[2];
+      za.bKt = f.bKt;
+      za.bMt = f.bMt;
+      za.inner = n1 * n2;
+      za.pitch = pitch;
+      za.n3 = f.n[2];
+      za.nt = f.n_t;
+      za.Z = zt_Z;
+      za.ws = ws;
+      za.wt = wt;
+      za.lo_t = f.lo_t;
+      za.hi_t = f.hi_t;
+      za.lo3 = f.lo[2];
+      za.hi3 = f.hi[2];
+      for (int r = 0; r < 4; ++r)
+        for (int w = 0; w < 2 * f.p_s + 1; ++w) za.i3[r][w] = f.lo[2] < f.hi[2] ? f.i3[r][w] : 0.f;
+      for (int w = 0; w < 2 * f.p_t + 1; ++w) {
+        za.iKt[w] = f.lo_t < f.hi_t ? f.iKt[w] : 0.f;
+        za.iMt[w] = f.lo_t < f.hi_t ? f.iMt[w] : 0.f;
+      }
+      return dispatch_zt(f.p_s, za, f.B, s);
+    }
+  }
   // direction 3
   if (f.d == 3) {
     ZArgs<T> za{};

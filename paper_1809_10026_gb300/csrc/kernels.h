@@ -44,6 +44,7 @@ struct SliceArgs {
   T *ls_last;                // two spatial directions: L_s x of the last time slice, per b
   const T *bM1, *bJ1, *bK1, *bM2, *bJ2, *bK2, *b2K2;
   long long slices;  // number of n2 x n1 slices
+  long long out_area;  // elements from one slice of out_m, out_j, out_k to the next (>= n1 n2)
   int n1, n2, n_t, row_stride;
   int lo2, hi2;      // rows [lo2, hi2) of the direction-2 bands are all equal (uniform knots)
 };
@@ -88,6 +89,8 @@ struct FusedA {
   // rows [lo, hi) of every band of a direction are identical (the interior
   // rows of uniform-knot Galerkin matrices); lo = hi = 0 when none are
   int lo[3], hi[3], lo_t, hi_t;
+  T iKt[2 * kFusedMaxP + 1], iMt[2 * kFusedMaxP + 1];  // host copy of the interior time band rows
+  T i3[4][2 * kFusedMaxP + 1];  // host copy of the interior rows of M, J, 2K, K of direction 3
 };
 // Largest run of rows around the middle row of an n x stride band array in
 // which every one of the given arrays has rows identical (bitwise) to its

@@ -35,6 +35,8 @@ struct AOps {
   T *pad_M[3] = {}, *pad_K[3] = {}, *pad_J[3] = {}, *pad_2K[3] = {};
   T *pad_Kt = nullptr, *pad_Mt = nullptr;
   int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0}, lo_t = 0, hi_t = 0;  // identical interior band rows
+  T int_Kt[2 * stls::kFusedMaxP + 1] = {}, int_Mt[2 * stls::kFusedMaxP + 1] = {};  // interior time rows (host)
+  T int_3[4][2 * stls::kFusedMaxP + 1] = {};  // interior rows of M, J, 2K, K of direction 3 (host)
   T *abuf[8] = {};
   T *ls_buf = nullptr;
 };
@@ -157,6 +159,11 @@ int upload_padded(stls_ctx *c, AOps<T> &A, int k, const stls::Dir1D &D, const st
   const std::vector<T> pJ = pad_band<T>(bJ, D.n, D.p, st, 1.0), p2K = pad_band<T>(bK, D.n, D.p, st, 2.0);
   const T *all[4] = {pM.data(), pK.data(), pJ.data(), p2K.data()};
   stls::toeplitz_rows<T>(all, 4, D.n, st, &A.lo[k], &A.hi[k]);
+  if (k == 2 && A.lo[k] < A.hi[k] && D.p <= stls::kFusedMaxP) {
+    const T *rows[4] = {pM.data(), pJ.data(), p2K.data(), pK.data()};
+    for (int b = 0; b < 4; ++b)
+      for (int w = 0; w < 2 * D.p + 1; ++w) A.int_3[b][w] = rows[b][static_cast<size_t>(A.lo[k]) * st + w];
+  }
   int rc = upload(c, &A.pad_M[k], pM);
   if (!rc) rc = upload(c, &A.pad_K[k], pK);
   if (!rc) rc = upload(c, &A.pad_J[k], pJ);
@@ -171,6 +178,11 @@ int upload_padded_time(stls_ctx *c, AOps<T> &A, const stls::Dir1D &Tm, const std
   const std::vector<T> pK = pad_band<T>(bKt, Tm.n, Tm.p, st, 1.0), pM = pad_band<T>(bMt, Tm.n, Tm.p, st, 1.0);
   const T *all[2] = {pK.data(), pM.data()};
   stls::toeplitz_rows<T>(all, 2, Tm.n, st, &A.lo_t, &A.hi_t);
+  if (A.lo_t < A.hi_t && Tm.p <= stls::kFusedMaxP)
+    for (int w = 0; w < 2 * Tm.p + 1; ++w) {
+      A.int_Kt[w] = pK[static_cast<size_t>(A.lo_t) * st + w];
+      A.int_Mt[w] = pM[static_cast<size_t>(A.lo_t) * st + w];
+    }
   int rc = upload(c, &A.pad_Kt, pK);
   if (!rc) rc = upload(c, &A.pad_Mt, pM);
   return rc;
@@ -457,6 +469,11 @@ stls::FusedA<T> fused_args(const stls_ctx *c, const AOps<T> &A) {
   }
   f.lo_t = A.lo_t;
   f.hi_t = A.hi_t;
+  for (int w = 0; w < 2 * stls::kFusedMaxP + 1; ++w) {
+    f.iKt[w] = A.int_Kt[w];
+    f.iMt[w] = A.int_Mt[w];
+    for (int b = 0; b < 4; ++b) f.i3[b][w] = A.int_3[b][w];
+  }
   for (int w = 0; w < 5; ++w) f.work[w] = A.abuf[w];
   f.ls_last = A.ls_buf;
   return f;
@@ -1107,7 +1124,13 @@ int stls_create(stls_ctx **out, const stls_params *prm, void *cuda_stream) {
     c->adf.ls_buf = reinterpret_cast<stls::dfloat *>(c->a64.ls_buf);
   }
   if (refine) {
-    for (int a = 0; a < 8 && !rc; ++a) rc = dev_alloc(c, &c->a32.abuf[a], BN);
+    // the direction-1/2 states of the FP32 product may be stored with every
+    // (t, i_3) slice padded to a multiple of 4 values
+    size_t BN32 = BN;
+    if (c->d == 3)
+      BN32 = std::max(BN, static_cast<size_t>(c->B) * c->n_t * c->n_s[2] *
+                              ((static_cast<size_t>(c->n_s[0]) * c->n_s[1] + 3) / 4 * 4));
+    for (int a = 0; a < 8 && !rc; ++a) rc = dev_alloc(c, &c->a32.abuf[a], BN32);
     if (!rc) rc = dev_alloc(c, &c->a32.ls_buf, BNs);
     float **iv[] = {&c->ri, &c->pi, &c->qi, &c->zi, &c->di};
     for (float **v : iv)
@@ -1202,6 +1225,17 @@ int stls_apply_A_df(stls_ctx *c, const double *x, double *y) {
   if (rc) return rc;
   STLS_LAUNCH(stls::launch_df_join(yd, y, c->N, c->B, nullptr, c->stream), "df_join");
   return STLS_OK;
+}
+
+int stls_apply_A_f32(stls_ctx *c, const float *x, float *y) {
+  if (c == nullptr) return STLS_EINVAL;
+  if (x == nullptr || y == nullptr || (reinterpret_cast<uintptr_t>(x) & 3u) != 0 ||
+      (reinterpret_cast<uintptr_t>(y) & 3u) != 0)
+    return set_err(c, STLS_EINVAL, "apply_A_f32: x or y is NULL or not 4-byte aligned");
+  if (x == y) return set_err(c, STLS_EINVAL, "apply_A_f32: x and y must not overlap");
+  if (!c->hs.prm.refine || c->a32.abuf[0] == nullptr)
+    return set_err(c, STLS_EINVAL, "apply_A_f32 needs a refinement context");
+  return apply_A_impl<float>(c, c->a32, x, y);
 }
 
 int stls_apply_precond(stls_ctx *c, const double *r, double *z) {

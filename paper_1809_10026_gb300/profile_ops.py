@@ -17,7 +17,7 @@ from paper_1809_10026_gb300 import synth
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--op", choices=["precond", "apply_A", "apply_A_df", "solve"], default="precond")
+    ap.add_argument("--op", choices=["precond", "apply_A", "apply_A_df", "apply_A_f32", "solve"], default="precond")
     ap.add_argument("--precision", choices=["fp64", "tf32", "bf16"], default="fp64")
     ap.add_argument("--d", type=int, default=3)
     ap.add_argument("--p", type=int, default=3)
@@ -33,6 +33,7 @@ def main():
                     inner_tol=a.inner_tol)
     x = torch.from_numpy(synth.uniform(S.N, 4, batch=a.batch)).cuda()
     y = torch.empty_like(x)
+    x32, y32 = x.float(), torch.empty_like(x, dtype=torch.float32)
 
     def run():
         if a.op == "precond":
@@ -41,6 +42,8 @@ def main():
             S.apply_A(x, out=y)
         elif a.op == "apply_A_df":
             S.apply_A_df(x, out=y)
+        elif a.op == "apply_A_f32":
+            S.apply_A_f32(x32, out=y32)
         else:
             S.solve(x, a.tol, 500, out=y)
 
