@@ -287,7 +287,12 @@ long long stls_launch_count(const stls_ctx *ctx);
  * events around each phase; stls_phase_times returns, for phase ids
  * 0 = A x in FP64, 1 = P^{-1} r, 2 = CG vector updates and reductions,
  * 3 = A x in FP32 (refinement form), the summed milliseconds and the number
- * of executions since the last reset (arrays of 4). */
+ * of executions since the last reset (arrays of 4).  Without timing, the
+ * refinement form runs each inner flexible-CG loop as one launch of a CUDA
+ * graph (a while node whose condition the last kernel of each step sets on
+ * the device: no host round trip per step); with timing on, the host drives
+ * the loop step by step so that the events can bracket each phase.  Both
+ * run the same kernels in the same order, so results are identical. */
 int stls_enable_timing(stls_ctx *ctx, int on);
 int stls_phase_times(stls_ctx *ctx, double *ms_out4, long long *count_out4);
 /* As stls_phase_times for the first min(n, 5) phase ids, adding

@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSM)
     if (!isfinite(tot[0])) {
       s.status = STLS_ENONFINITE;
       s.active = 0;
-    } else if (s.rel_res <= tol) {
+    } else if (s.rel_res <= (tol >= 0.0 ? tol : s.tol_in)) {
       s.active = 0;
     }
   }
@@ -297,6 +297,7 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSM)
                    const T *__restrict__ q, long long N, int flexible, int first, CGState *st,
                    RedWork rw) {
   const int b = blockIdx.y;
+  if (first < 0) first = st[b].iters == 0;
   const T *zb = z + static_cast<size_t>(b) * N, *rb = r + static_cast<size_t>(b) * N;
   const T *qb = q + static_cast<size_t>(b) * N;
   const bool need_zq = flexible && !first;
@@ -379,6 +380,7 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSM)
                 CGState *st, T *__restrict__ x, unsigned *tickets) {
   const int b = blockIdx.y;
   if (!st[b].active) return;
+  if (first < 0) first = st[b].iters == 0;
   const T beta = static_cast<T>(st[b].beta);
   const T *zb = z + static_cast<size_t>(b) * N;
   T *pb = p + static_cast<size_t>(b) * N;
@@ -479,7 +481,8 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSM)
 // norm is accumulated by Dot2f.
 __global__ void __launch_bounds__(kThreads, kBlocksPerSM)
     ir_start_kernel(const double *__restrict__ r64, float *__restrict__ r32, float *__restrict__ d,
-                    long long N, const CGState *outer, CGState *inner, RedWork rw, PadOut pad) {
+                    long long N, const CGState *outer, CGState *inner, RedWork rw, PadOut pad, double eta,
+                    int limit) {
   const int b = blockIdx.y;
   const int k = ptx::df_scale_exp(outer[b].rr);
   const double *rb = r64 + static_cast<size_t>(b) * N;
@@ -521,8 +524,17 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSM)
     s.status = 0;
     s.rel_res = 1.0;
     s.alpha = s.beta = s.pq = s.rz = 0.0;
+    s.tol_in = eta;
+    s.limit = limit;
     s.active = outer[b].active && tot[0] > 0.0;
   }
+}
+
+__global__ void inner_cond_kernel(const CGState *st, int B, cudaGraphConditionalHandle h) {
+  unsigned go = 0;
+  for (int b = 0; b < B; ++b)
+    if (st[b].active && st[b].iters < st[b].limit) go = 1;
+  cudaGraphSetConditional(h, go);
 }
 
 // u += 2^k d (the scaling of ir_start undone exactly) for the right-hand sides
@@ -830,11 +842,16 @@ cudaError_t launch_cg_xr_pad(float *x, float *r, const float *p, const float *q,
   return cudaGetLastError();
 }
 cudaError_t launch_ir_start(const double *r64, float *r32, float *d, long long N, int B, const CGState *outer,
-                            CGState *inner, RedWork rw, float *rpad, int n0, int np0, cudaStream_t s) {
+                            CGState *inner, RedWork rw, float *rpad, int n0, int np0, double eta, int limit,
+                            cudaStream_t s) {
   if (rpad != nullptr && (n0 < 1 || np0 < n0 || N % n0 != 0 || static_cast<double>(N / n0) * np0 >= 4294967296.0))
     return cudaErrorInvalidValue;
   const PadOut pad{rpad, rpad != nullptr ? n0 : 1, rpad != nullptr ? np0 : 1};
-  ir_start_kernel<<<dim3(rw.grid, B), kThreads, 0, s>>>(r64, r32, d, N, outer, inner, rw, pad);
+  ir_start_kernel<<<dim3(rw.grid, B), kThreads, 0, s>>>(r64, r32, d, N, outer, inner, rw, pad, eta, limit);
+  return cudaGetLastError();
+}
+cudaError_t launch_inner_cond(const CGState *st, int B, cudaGraphConditionalHandle h, cudaStream_t s) {
+  inner_cond_kernel<<<1, 1, 0, s>>>(st, B, h);
   return cudaGetLastError();
 }
 cudaError_t launch_ir_correct(double *u, const float *d, dfloat *udf, long long N, int B, const CGState *outer,

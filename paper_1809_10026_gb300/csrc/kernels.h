@@ -149,6 +149,8 @@ struct CGState {
   double rz, pq, alpha, beta, rr, nF2, rel_res, true_rr;
   int active, iters, status, df_iters;  // df_iters: provisional double-float residuals
   int xpend;  // deferred x update: alpha p of the last x, r update is still owed to x
+  int limit;      // inner solves: iteration cap of this outer step (graph loop condition)
+  double tol_in;  // inner solves: relative-residual target (kernels given tol < 0 read it)
 };
 struct RedWork {
   double *partials;    // [batch][grid][2]
@@ -172,6 +174,8 @@ cudaError_t launch_cg_xr(T *x, T *r, const T *p, const T *q, long long N, int B,
 // defer != 0: x is not updated here (see launch_cg_p).
 cudaError_t launch_cg_xr_pad(float *x, float *r, const float *p, const float *q, long long N, int B, double tol,
                              CGState *st, RedWork rw, float *rpad, int n0, int np0, int defer, cudaStream_t s);
+// first < 0 (launch_cg_beta, launch_cg_p): the first step of the CG loop is
+// the one with st.iters == 0, read on the device (a captured loop body).
 template <typename T>
 cudaError_t launch_cg_beta(const T *z, const T *r, const T *q, long long N, int B, int flexible, int first,
                            CGState *st, RedWork rw, cudaStream_t s);
@@ -188,8 +192,13 @@ cudaError_t launch_cg_x_pending(float *x, const float *p, long long N, int B, co
 // convergence test.
 // (rpad != NULL: also r32 rounded to TF32 into rows of n0 values np0 apart,
 // as launch_cg_xr_pad writes them.)
+// The inner states also get tol_in = eta and limit = the iteration cap.
 cudaError_t launch_ir_start(const double *r64, float *r32, float *d, long long N, int B, const CGState *outer,
-                            CGState *inner, RedWork rw, float *rpad, int n0, int np0, cudaStream_t s);
+                            CGState *inner, RedWork rw, float *rpad, int n0, int np0, double eta, int limit,
+                            cudaStream_t s);
+// One thread: sets the while-loop condition of a graph to "some right-hand
+// side is active with iters < limit".
+cudaError_t launch_inner_cond(const CGState *st, int B, cudaGraphConditionalHandle h, cudaStream_t s);
 // u += 2^k d (k: exponent of ||r64||, as ir_start scaled); with udf != NULL
 // also writes launch_df_split's image of the new u (scale from outer).
 cudaError_t launch_ir_correct(double *u, const float *d, dfloat *udf, long long N, int B, const CGState *outer,

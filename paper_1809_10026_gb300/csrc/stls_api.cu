@@ -75,6 +75,12 @@ struct stls_ctx {
   std::vector<std::vector<double>> hist;  // relative residuals of the last solve, per RHS
   long long launches = 0;
   std::string err;
+  // inner FP32 loop of the refinement form as a CUDA graph: a while node whose
+  // body is one CG step, its condition set on the device (built on first use)
+  cudaGraph_t ig_graph = nullptr;
+  cudaGraphExec_t ig_exec = nullptr;
+  long long ig_body_launches = 0;  // kernels in one body
+  bool ig_failed = false;          // the graph could not be built: host-driven loop
   // timing
   bool timing = false;
   double phase_ms[5] = {0, 0, 0, 0, 0};
@@ -798,6 +804,87 @@ int solve_impl(stls_ctx *c, const double *F, double *u, double tol, int maxit, s
 // vectors and A p, the tensor-core preconditioner, inner products compensated
 // in FP32 per thread and summed in FP64) until its residual falls below the
 // inner tolerance, and update u += 2^k d in FP64.
+// One step of the inner flexible CG of the refinement form, as the body of a
+// graph while loop: z = P r, beta and p (first step: st.iters == 0, read on
+// the device), q = A p with alpha, then x, r and the loop condition.  The
+// inner tolerance comes from the state (ir_start wrote it).
+int inner_graph_body(stls_ctx *c, float *rpad, int pad_n0, int pad_np0, cudaGraphConditionalHandle h) {
+  const long long N = c->N;
+  const int B = c->B;
+  if (rpad != nullptr) {
+    c->launches += stls::tc_fd_launch_count(c->tc) - 1;
+    STLS_CK(stls::tc_fd_apply_f32_padded(c->tc, c->zi, c->stream), "tensor-core FD apply");
+  } else {
+    c->launches += stls::tc_fd_launch_count(c->tc);
+    STLS_CK(stls::tc_fd_apply_f32(c->tc, c->ri, c->zi, c->stream), "tensor-core FD apply");
+  }
+  STLS_LAUNCH(stls::launch_cg_beta<float>(c->zi, c->ri, c->qi, N, B, 1, -1, c->st_in, c->rw, c->stream),
+              "cg_beta");
+  STLS_LAUNCH(stls::launch_cg_p<float>(c->zi, c->pi, N, B, -1, c->st_in, c->stream,
+                                       rpad != nullptr ? c->di : nullptr, c->rw.tickets),
+              "cg_p");
+  const int rc = apply_A_f32_alpha(c, c->pi, c->qi);
+  if (rc) return rc;
+  if (rpad != nullptr)
+    STLS_LAUNCH(stls::launch_cg_xr_pad(c->di, c->ri, c->pi, c->qi, N, B, -1.0, c->st_in, c->rw, rpad, pad_n0,
+                                       pad_np0, 1, c->stream),
+                "cg_xr");
+  else
+    STLS_LAUNCH(stls::launch_cg_xr<float>(c->di, c->ri, c->pi, c->qi, N, B, -1.0, c->st_in, c->rw, c->stream),
+                "cg_xr");
+  STLS_LAUNCH(stls::launch_inner_cond(c->st_in, B, h, c->stream), "inner_cond");
+  return STLS_OK;
+}
+
+// Builds the inner-loop graph (a while node around inner_graph_body, captured
+// on a private stream).  Returns false, and marks the context, when the graph
+// cannot be built: the solve then drives the loop from the host.
+bool build_inner_graph(stls_ctx *c, float *rpad, int pad_n0, int pad_np0) {
+  cudaGraph_t g = nullptr;
+  cudaGraphConditionalHandle h = 0;
+  cudaStream_t cap = nullptr;
+  bool ok = cudaGraphCreate(&g, 0) == cudaSuccess &&
+            cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) == cudaSuccess;
+  cudaGraphNodeParams cp = {};
+  cudaGraphNode_t node = nullptr;
+  if (ok) {
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    ok = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp) == cudaSuccess;
+  }
+  if (ok) {
+    cudaStream_t user = c->stream;
+    const long long l0 = c->launches;
+    c->stream = cap;
+    if (cudaStreamBeginCaptureToGraph(cap, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      const int rc = inner_graph_body(c, rpad, pad_n0, pad_np0, h);
+      cudaGraph_t body = nullptr;
+      ok = cudaStreamEndCapture(cap, &body) == cudaSuccess && rc == STLS_OK;
+    } else {
+      ok = false;
+    }
+    c->stream = user;
+    c->ig_body_launches = c->launches - l0;
+    c->launches = l0;
+  }
+  if (ok) ok = cudaGraphInstantiate(&c->ig_exec, g, 0) == cudaSuccess;
+  if (cap != nullptr) cudaStreamDestroy(cap);
+  if (!ok) {
+    if (g != nullptr) cudaGraphDestroy(g);
+    c->ig_exec = nullptr;
+    c->ig_failed = true;
+    cudaGetLastError();  // clear the failed calls' error state
+    c->err.clear();
+    return false;
+  }
+  c->ig_graph = g;
+  return true;
+}
+
 int solve_ir_impl(stls_ctx *c, const double *F, double *u, double tol, int maxit, stls_solve_info *info) {
   if (!(tol >= 0.0) || maxit < 0) return set_err(c, STLS_EINVAL, "tol must be >= 0 and maxit >= 0");
   if (check_ptr(c, F, "F") || check_ptr(c, u, "u")) return STLS_EINVAL;
@@ -882,51 +969,21 @@ int solve_ir_impl(stls_ctx *c, const double *F, double *u, double tol, int maxit
     }
     // ---- inner flexible CG in FP32 on A d = r 2^-k ----
     ph = phase_begin(c, 2);
-    STLS_LAUNCH(stls::launch_ir_start(r64, c->ri, c->di, N, B, c->st, c->st_in, c->rw, rpad, pad_n0, pad_np0,
-                                      c->stream),
+    const int budget = std::min(maxit - total_inner, kMaxInnerPerOuter);
+    STLS_LAUNCH(stls::launch_ir_start(r64, c->ri, c->di, N, B, c->st, c->st_in, c->rw, rpad, pad_n0, pad_np0, eta,
+                                      budget, c->stream),
                 "ir_start");
     phase_end(c, ph);
-    ph = phase_begin(c, 1);
-    if (rpad != nullptr) {  // ir_start wrote r into the preconditioner's input rows
-      c->launches += stls::tc_fd_launch_count(c->tc) - 1;
-      STLS_CK(stls::tc_fd_apply_f32_padded(c->tc, c->zi, c->stream), "tensor-core FD apply");
+    // The inner loop runs as one graph launch (no host round trip per step)
+    // unless phases are being timed or the graph could not be built.
+    const bool graph = !c->timing && !c->ig_failed &&
+                       (c->ig_exec != nullptr || build_inner_graph(c, rpad, pad_n0, pad_np0));
+    if (graph) {
+      STLS_CK(cudaGraphLaunch(c->ig_exec, c->stream), "inner CG graph");
     } else {
-      c->launches += stls::tc_fd_launch_count(c->tc);
-      STLS_CK(stls::tc_fd_apply_f32(c->tc, c->ri, c->zi, c->stream), "tensor-core FD apply");
-    }
-    phase_end(c, ph);
-    ph = phase_begin(c, 2);
-    STLS_LAUNCH(stls::launch_cg_beta<float>(c->zi, c->ri, c->qi, N, B, 1, 1, c->st_in, c->rw, c->stream),
-                "cg_beta");
-    STLS_LAUNCH(stls::launch_cg_p<float>(c->zi, c->pi, N, B, 1, c->st_in, c->stream), "cg_p");
-    phase_end(c, ph);
-    const int budget = std::min(maxit - total_inner, kMaxInnerPerOuter);
-    for (int it = 1; it <= budget; ++it) {
-      ph = phase_begin(c, 3);
-      rc = apply_A_f32_alpha(c, c->pi, c->qi);  // q = A p and alpha
-      if (rc) return rc;
-      phase_end(c, ph);
-      ph = phase_begin(c, 2);
-      if (rpad != nullptr)  // r also goes straight into the TF32 preconditioner's input rows; d += a p deferred
-        STLS_LAUNCH(stls::launch_cg_xr_pad(c->di, c->ri, c->pi, c->qi, N, B, eta, c->st_in, c->rw, rpad, pad_n0,
-                                           pad_np0, 1, c->stream),
-                    "cg_xr");
-      else
-        STLS_LAUNCH(stls::launch_cg_xr<float>(c->di, c->ri, c->pi, c->qi, N, B, eta, c->st_in, c->rw, c->stream),
-                    "cg_xr");
-      phase_end(c, ph);
-      STLS_CK(cudaMemcpyAsync(inner_host.data(), c->st_in, sizeof(CGState) * B, cudaMemcpyDeviceToHost,
-                              c->stream),
-              "state copy");
-      STLS_CK(cudaStreamSynchronize(c->stream), "sync");
-      if (stls::tc_fd_error(c->tc))
-        return set_err(c, STLS_ECUDA, "tensor-core FD apply: a bounded mbarrier wait timed out");
-      bool inner_any = false;
-      for (int b = 0; b < B; ++b) inner_any = inner_any || inner_host[b].active;
-      if (!inner_any) break;
       ph = phase_begin(c, 1);
-      if (rpad != nullptr) {
-        c->launches += stls::tc_fd_launch_count(c->tc) - 1;  // no padding pass
+      if (rpad != nullptr) {  // ir_start wrote r into the preconditioner's input rows
+        c->launches += stls::tc_fd_launch_count(c->tc) - 1;
         STLS_CK(stls::tc_fd_apply_f32_padded(c->tc, c->zi, c->stream), "tensor-core FD apply");
       } else {
         c->launches += stls::tc_fd_launch_count(c->tc);
@@ -934,17 +991,66 @@ int solve_ir_impl(stls_ctx *c, const double *F, double *u, double tol, int maxit
       }
       phase_end(c, ph);
       ph = phase_begin(c, 2);
-      STLS_LAUNCH(stls::launch_cg_beta<float>(c->zi, c->ri, c->qi, N, B, 1, 0, c->st_in, c->rw, c->stream),
+      STLS_LAUNCH(stls::launch_cg_beta<float>(c->zi, c->ri, c->qi, N, B, 1, 1, c->st_in, c->rw, c->stream),
                   "cg_beta");
-      STLS_LAUNCH(stls::launch_cg_p<float>(c->zi, c->pi, N, B, 0, c->st_in, c->stream,
-                                           rpad != nullptr ? c->di : nullptr, c->rw.tickets),
-                  "cg_p");
+      STLS_LAUNCH(stls::launch_cg_p<float>(c->zi, c->pi, N, B, 1, c->st_in, c->stream), "cg_p");
       phase_end(c, ph);
+      for (int it = 1; it <= budget; ++it) {
+        ph = phase_begin(c, 3);
+        rc = apply_A_f32_alpha(c, c->pi, c->qi);  // q = A p and alpha
+        if (rc) return rc;
+        phase_end(c, ph);
+        ph = phase_begin(c, 2);
+        if (rpad != nullptr)  // r also goes straight into the TF32 preconditioner's input rows; d += a p deferred
+          STLS_LAUNCH(stls::launch_cg_xr_pad(c->di, c->ri, c->pi, c->qi, N, B, eta, c->st_in, c->rw, rpad, pad_n0,
+                                             pad_np0, 1, c->stream),
+                      "cg_xr");
+        else
+          STLS_LAUNCH(stls::launch_cg_xr<float>(c->di, c->ri, c->pi, c->qi, N, B, eta, c->st_in, c->rw, c->stream),
+                      "cg_xr");
+        phase_end(c, ph);
+        STLS_CK(cudaMemcpyAsync(inner_host.data(), c->st_in, sizeof(CGState) * B, cudaMemcpyDeviceToHost,
+                                c->stream),
+                "state copy");
+        STLS_CK(cudaStreamSynchronize(c->stream), "sync");
+        if (stls::tc_fd_error(c->tc))
+          return set_err(c, STLS_ECUDA, "tensor-core FD apply: a bounded mbarrier wait timed out");
+        bool inner_any = false;
+        for (int b = 0; b < B; ++b) inner_any = inner_any || inner_host[b].active;
+        if (!inner_any) break;
+        ph = phase_begin(c, 1);
+        if (rpad != nullptr) {
+          c->launches += stls::tc_fd_launch_count(c->tc) - 1;  // no padding pass
+          STLS_CK(stls::tc_fd_apply_f32_padded(c->tc, c->zi, c->stream), "tensor-core FD apply");
+        } else {
+          c->launches += stls::tc_fd_launch_count(c->tc);
+          STLS_CK(stls::tc_fd_apply_f32(c->tc, c->ri, c->zi, c->stream), "tensor-core FD apply");
+        }
+        phase_end(c, ph);
+        ph = phase_begin(c, 2);
+        STLS_LAUNCH(stls::launch_cg_beta<float>(c->zi, c->ri, c->qi, N, B, 1, 0, c->st_in, c->rw, c->stream),
+                    "cg_beta");
+        STLS_LAUNCH(stls::launch_cg_p<float>(c->zi, c->pi, N, B, 0, c->st_in, c->stream,
+                                             rpad != nullptr ? c->di : nullptr, c->rw.tickets),
+                    "cg_p");
+        phase_end(c, ph);
+      }
     }
     if (rpad != nullptr) {  // x updates deferred by the last CG updates
       ph = phase_begin(c, 2);
       STLS_LAUNCH(stls::launch_cg_x_pending(c->di, c->pi, N, B, c->st_in, c->stream), "cg_x_pending");
       phase_end(c, ph);
+    }
+    if (graph) {  // the inner states after the loop, and the kernels it ran
+      STLS_CK(cudaMemcpyAsync(inner_host.data(), c->st_in, sizeof(CGState) * B, cudaMemcpyDeviceToHost,
+                              c->stream),
+              "state copy");
+      STLS_CK(cudaStreamSynchronize(c->stream), "sync");
+      if (stls::tc_fd_error(c->tc))
+        return set_err(c, STLS_ECUDA, "tensor-core FD apply: a bounded mbarrier wait timed out");
+      int steps = 1;
+      for (int b = 0; b < B; ++b) steps = std::max(steps, inner_host[b].iters);
+      c->launches += c->ig_body_launches * steps;
     }
     int its = 0;
     double inner_worst = 0.0;
@@ -1024,6 +1130,8 @@ const char *stls_last_error(const stls_ctx *ctx) {
 void stls_destroy(stls_ctx *ctx) {
   if (ctx == nullptr) return;
   cudaStreamSynchronize(ctx->stream);
+  if (ctx->ig_exec) cudaGraphExecDestroy(ctx->ig_exec);
+  if (ctx->ig_graph) cudaGraphDestroy(ctx->ig_graph);
   stls::tc_fd_destroy(ctx->tc);
   for (void *v : ctx->allocations) cudaFree(v);
   if (ctx->st_host) cudaFreeHost(ctx->st_host);

@@ -28,6 +28,8 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--refine", action="store_true", help="iterative-refinement form (mixed precisions)")
     ap.add_argument("--inner-tol", type=float, default=0.0, help="inner tolerance of the refinement form (0: adaptive)")
+    ap.add_argument("--no-phases", action="store_true",
+                    help="solve: no per-phase timing (the refinement form then runs its inner loop as one graph)")
     a = ap.parse_args()
     S = stls.Solver(a.d, a.p, a.n_el, precision=a.precision, batch=a.batch, refine=a.refine,
                     inner_tol=a.inner_tol)
@@ -57,7 +59,7 @@ def main():
         run = run_solve  # noqa: F811
     for _ in range(a.warmup):
         run()
-    if a.op == "solve":
+    if a.op == "solve" and not a.no_phases:
         S.enable_timing(True)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -73,6 +75,7 @@ def main():
            "launches_per_rep": (S.launch_count() - l0) / a.reps}
     if info is not None:
         out["info"] = info[0]
+    if info is not None and not a.no_phases:
         out["phases_ms_per_rep"] = {k: (v[0] / a.reps, v[1] / a.reps) for k, v in S.phase_times().items()}
     print(json.dumps(out))
 
