@@ -214,13 +214,12 @@ def timed_solves(S, F, u, tol, steps, warmup, world, timing):
 TRAFFIC = {
     # fused BF16 FD apply with FP32 in/out: 5 kernels, 234.8 MB read + 19.1 MB written
     ("precond", "bf16", True): 253888256,
-    # TF32 FD apply inside the inner loop: not captured since its passes fetch the last K
-    # values in no-swizzle 4-value boxes
-    ("precond", "tf32", True): None,
-    # FP32 A x of the inner loop (slice, direction 3, time with (p, A p)): 509.1 MB read + 307.8 MB
-    # written; the same kernels serve both refinement forms
-    ("apply_A_f32", "tf32", True): 816874240,
-    ("apply_A_f32", "bf16", True): 816874240,
+    # TF32 FD apply inside the inner loop: 8 rotation passes, 649.7 MB read + 133.9 MB written
+    ("precond", "tf32", True): 783665536,
+    # FP32 A x of the inner loop (slice kernel, fused direction 3 + time with (p, A p)):
+    # 398.7 MB read + 211.3 MB written; the same kernels serve both refinement forms
+    ("apply_A_f32", "tf32", True): 610040042,
+    ("apply_A_f32", "bf16", True): 610040042,
 }
 
 
