@@ -206,8 +206,12 @@ int stls_solve(stls_ctx *ctx, const double *F, double *u, double tol, int maxit,
                stls_solve_info *info);
 
 /* As stls_solve, with F and u in HOST memory (B x N each): copies F to the
- * device, solves, copies u back, all on the context's stream.  Pinned host
- * memory gives the fastest copies. */
+ * device, solves, copies u back, and returns when u_host holds the result.
+ * Pinned host memory gives the fastest copies.  In the refinement form the
+ * copy of u runs on a second stream of the context while the FP64 residual
+ * that may confirm convergence is computed (u no longer changes then), and is
+ * repeated if a further outer step changes u; u_host may therefore be written
+ * more than once during the call. */
 int stls_solve_host(stls_ctx *ctx, const double *F_host, double *u_host, double tol,
                     int maxit, stls_solve_info *info);
 

@@ -81,6 +81,11 @@ struct stls_ctx {
   cudaGraphExec_t ig_exec = nullptr;
   long long ig_body_launches = 0;  // kernels in one body
   bool ig_failed = false;          // the graph could not be built: host-driven loop
+  // stls_solve_host: u's copy to the host overlaps the FP64 residual that
+  // confirms convergence (side stream); redone if a later step changes u
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_u = nullptr, ev_copied = nullptr;
+  bool early_issued = false, early_final = false;
   // timing
   bool timing = false;
   double phase_ms[5] = {0, 0, 0, 0, 0};
@@ -885,7 +890,12 @@ bool build_inner_graph(stls_ctx *c, float *rpad, int pad_n0, int pad_np0) {
   return true;
 }
 
-int solve_ir_impl(stls_ctx *c, const double *F, double *u, double tol, int maxit, stls_solve_info *info) {
+// u_host_early != NULL (stls_solve_host): before each FP64 residual, u (final
+// unless that residual asks for another step) is copied to u_host_early on
+// c->copy_stream, overlapping the FP64 A x; c->early_final tells whether the
+// last copy holds the returned u.
+int solve_ir_impl(stls_ctx *c, const double *F, double *u, double tol, int maxit, stls_solve_info *info,
+                  double *u_host_early = nullptr) {
   if (!(tol >= 0.0) || maxit < 0) return set_err(c, STLS_EINVAL, "tol must be >= 0 and maxit >= 0");
   if (check_ptr(c, F, "F") || check_ptr(c, u, "u")) return STLS_EINVAL;
   const long long N = c->N;
@@ -913,6 +923,15 @@ int solve_ir_impl(stls_ctx *c, const double *F, double *u, double tol, int maxit
   const double kDfMargin = 100.0, kDfFloor = 1e-8, kContractFloor = 4e-4;
   double *xdf_buf = c->p;  // FP64 CG vectors, unused by the refinement form
   auto fp64_residual = [&](int count) -> int {
+    if (u_host_early != nullptr && !c->early_final) {
+      STLS_CK(cudaEventRecord(c->ev_u, c->stream), "event");
+      STLS_CK(cudaStreamWaitEvent(c->copy_stream, c->ev_u, 0), "event wait");
+      STLS_CK(cudaMemcpyAsync(u_host_early, u, sizeof(double) * static_cast<size_t>(B) * N, cudaMemcpyDeviceToHost,
+                              c->copy_stream),
+              "D2H copy of u");
+      STLS_CK(cudaEventRecord(c->ev_copied, c->copy_stream), "event");
+      c->early_issued = c->early_final = true;
+    }
     int ph2 = phase_begin(c, 0);
     int rc2 = apply_A_impl<double>(c, c->a64, u, q64);
     if (rc2) return rc2;
@@ -1065,6 +1084,7 @@ int solve_ir_impl(stls_ctx *c, const double *F, double *u, double tol, int maxit
     stls::dfloat *xdf = reinterpret_cast<stls::dfloat *>(xdf_buf), *ydf = reinterpret_cast<stls::dfloat *>(q64);
     ph = phase_begin(c, 2);
     STLS_LAUNCH(stls::launch_ir_correct(u, c->di, use_df ? xdf : nullptr, N, B, c->st, c->stream), "ir_correct");
+    c->early_final = false;  // u changed since any earlier copy
     phase_end(c, ph);
     if (use_df) {  // the correction kernel wrote the double-float image of u
       ph = phase_begin(c, 4);
@@ -1130,6 +1150,9 @@ const char *stls_last_error(const stls_ctx *ctx) {
 void stls_destroy(stls_ctx *ctx) {
   if (ctx == nullptr) return;
   cudaStreamSynchronize(ctx->stream);
+  if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+  if (ctx->ev_u) cudaEventDestroy(ctx->ev_u);
+  if (ctx->ev_copied) cudaEventDestroy(ctx->ev_copied);
   if (ctx->ig_exec) cudaGraphExecDestroy(ctx->ig_exec);
   if (ctx->ig_graph) cudaGraphDestroy(ctx->ig_graph);
   stls::tc_fd_destroy(ctx->tc);
@@ -1364,11 +1387,23 @@ int stls_solve_host(stls_ctx *c, const double *F_host, double *u_host, double to
   NvtxScope range("stls_solve_host");
   if (c == nullptr || F_host == nullptr || u_host == nullptr) return set_err(c, STLS_EINVAL, "NULL argument");
   const size_t bytes = sizeof(double) * static_cast<size_t>(c->B) * c->N;
+  if (c->hs.prm.refine && c->copy_stream == nullptr) {
+    STLS_CK(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking), "copy stream");
+    STLS_CK(cudaEventCreateWithFlags(&c->ev_u, cudaEventDisableTiming), "event");
+    STLS_CK(cudaEventCreateWithFlags(&c->ev_copied, cudaEventDisableTiming), "event");
+  }
+  c->early_issued = c->early_final = false;
   STLS_CK(cudaMemcpyAsync(c->dF, F_host, bytes, cudaMemcpyHostToDevice, c->stream), "H2D copy of F");
-  int rc = c->hs.prm.refine ? solve_ir_impl(c, c->dF, c->du, tol, maxit, info)
+  int rc = c->hs.prm.refine ? solve_ir_impl(c, c->dF, c->du, tol, maxit, info, u_host)
                             : solve_impl(c, c->dF, c->du, tol, maxit, info);
-  if (rc != STLS_OK && rc != STLS_ENOTCONV && rc != STLS_EBREAKDOWN && rc != STLS_ENONFINITE) return rc;
-  STLS_CK(cudaMemcpyAsync(u_host, c->du, bytes, cudaMemcpyDeviceToHost, c->stream), "D2H copy of u");
+  // an early copy of u (refinement form) ends before anything else writes u_host
+  if (c->early_issued) STLS_CK(cudaStreamWaitEvent(c->stream, c->ev_copied, 0), "event wait");
+  if (rc != STLS_OK && rc != STLS_ENOTCONV && rc != STLS_EBREAKDOWN && rc != STLS_ENONFINITE) {
+    cudaStreamSynchronize(c->stream);
+    return rc;
+  }
+  if (!c->early_final)
+    STLS_CK(cudaMemcpyAsync(u_host, c->du, bytes, cudaMemcpyDeviceToHost, c->stream), "D2H copy of u");
   STLS_CK(cudaStreamSynchronize(c->stream), "sync");
   return rc;
 }

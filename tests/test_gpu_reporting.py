@@ -50,6 +50,28 @@ def test_solve_host_matches_device_solve(kw):
         assert np.linalg.norm(u_host.reshape(B, -1)[b] - ref) <= 1e-8 * np.linalg.norm(ref)
 
 
+@pytest.mark.parametrize("tol", [1e-8, 1e-11])
+def test_solve_host_refinement_copy_overlap(tol):
+    """Refinement form: stls_solve_host copies u to the host while the FP64
+    residual that may confirm convergence runs, and again if a later outer
+    step changes u.  At 1e-11 several outer steps take an FP64 residual, so
+    early copies are superseded; the host u must still equal the device
+    solve's bit for bit, on repeated calls into the same buffer."""
+    prob = STProblem(3, 3, 12)
+    S = _solver(3, 3, 12, precision="tf32", refine=True)
+    F = synth.uniform(prob.N, 23)
+    u_dev, info_d = S.solve(_cuda(F), tol=tol, maxit=400)
+    u_dev = u_dev.cpu().numpy()
+    assert info_d[0]["status"] == "ok" and info_d[0]["outer"] >= (3 if tol < 1e-10 else 2)
+    Fh = torch.from_numpy(F).pin_memory()
+    uh = torch.full_like(Fh, float("nan")).pin_memory()
+    for _ in range(2):
+        info_h = S.solve_host_ptr(Fh.data_ptr(), uh.data_ptr(), tol=tol, maxit=400)
+        assert info_h[0]["iters"] == info_d[0]["iters"] and info_h[0]["outer"] == info_d[0]["outer"]
+        assert np.array_equal(uh.numpy(), u_dev)
+        uh.fill_(float("nan"))
+
+
 def test_context_factors_and_launch_count():
     """stls_get_factor returns the context's copies of the host setup's 1D
     factors (bitwise those of stls_host_factor), and the launch counter
