@@ -569,7 +569,10 @@ __global__ void __launch_bounds__(kAThreads) tpass_kernel(const __grid_constant_
 // emits y = K_t (M_s x) + M_t (J_s x) (+ L_s x on the last slice) for the time
 // row P behind: 4 vector passes instead of the 8 of a direction-3 pass and a
 // time pass (5 with the fused (p, A p)).  Each sum of several band products is
-// formed as independent FMA chains, one per band, added at the end.  The band
+// formed as independent FMA chains, one per band, added at the end; two chains
+// over the same band length run as one chain of paired FP32 FMAs (__ffma2_rn:
+// M3 m with M3 j', and K_t (M_s x) with M_t (J_s x) from a window of pairs),
+// which halves their instructions and rounds like two separate chains.  The band
 // rows shared by the interior rows of direction 3 and of time are kernel
 // parameters (constant bank); warps of a boundary row i_3 read theirs from
 // the band arrays, and time groups touching a boundary row or the last slice
@@ -586,8 +589,9 @@ struct ZTArgs {
   AlphaFuse fuse;
   const float *bM3, *bJ3, *bK3, *b2K3;  // padded direction-3 bands (row stride ws)
   const float *bKt, *bMt;               // padded time bands (row stride wt)
-  float iKt[kZtMaxW], iMt[kZtMaxW];     // the time band rows [lo_t, hi_t) all equal these
+  float2 iKM[kZtMaxW];                  // (K_t, M_t) of the time band rows [lo_t, hi_t), all equal
   float i3[4][kZtMaxW];                 // rows [lo3, hi3) of M3, J3, 2 K3, K3 all equal these
+  float2 i3mm[kZtMaxW];                 // (M3, M3) of that row, for paired products
   long long inner, pitch;               // n1 n2 and its rounding up to a multiple of 4
   int n3, nt, Z, ws, wt, lo3, hi3, lo_t, hi_t;
 };
@@ -665,9 +669,9 @@ __global__ void __launch_bounds__(kZtCols * kZtMaxZ, 2) zt_kernel(const __grid_c
   };
 #pragma unroll
   for (int e = 0; e < D; ++e) issue(e, e);
-  float wMs[W], wJs[W];
+  float2 win[W];  // time window of (M_s x, J_s x): one paired FMA per band term
 #pragma unroll
-  for (int w = 0; w < W; ++w) wMs[w] = wJs[w] = 0.f;
+  for (int w = 0; w < W; ++w) win[w] = make_float2(0.f, 0.f);
   float ls = 0.f;  // L_s x of the last time slice
   Dot2f acc;
   int slot = 0;
@@ -677,7 +681,7 @@ __global__ void __launch_bounds__(kZtCols * kZtMaxZ, 2) zt_kernel(const __grid_c
     constexpr bool FAST = decltype(fast)::value;
     const int y = tt - P;
     const bool emit = FAST || (y >= 0 && y < nt);
-    float pv = 0.f;  // p of the emitted row: staged with the slice, or loaded in the last P steps
+    [[maybe_unused]] float pv = 0.f;  // p of the emitted row: staged with the slice, or loaded in the last P steps
     if constexpr (FUSE)
       if (!FAST && tt >= nt && emit && act) pv = a.fuse.p[obase + static_cast<long long>(y) * slice];
     float ms = 0.f, js = 0.f;
@@ -695,15 +699,17 @@ __global__ void __launch_bounds__(kZtCols * kZtMaxZ, 2) zt_kernel(const __grid_c
         kv[w] = sm[2 * arr_floats + w * kZtCols];
       }
       if (!bdry) {
-        float j1 = 0.f, j2 = 0.f, j3 = 0.f;
+        // M3 m and M3 j' as the two halves of one paired FMA chain
+        float2 mj = make_float2(0.f, 0.f);
+        float j2 = 0.f, j3 = 0.f;
 #pragma unroll
         for (int w = 0; w < W; ++w) {
-          ms = fmaf(a.i3[0][w], mv[w], ms);
-          j1 = fmaf(a.i3[0][w], jv[w], j1);
+          mj = __ffma2_rn(a.i3mm[w], make_float2(mv[w], jv[w]), mj);
           j2 = fmaf(a.i3[1][w], mv[w], j2);
           j3 = fmaf(a.i3[2][w], kv[w], j3);
         }
-        js = (j1 + j2) + j3;
+        ms = mj.x;
+        js = (mj.y + j2) + j3;
         if (!FAST && tt == nt - 1) {
           float l1 = 0.f, l2 = 0.f;
 #pragma unroll
@@ -721,21 +727,19 @@ __global__ void __launch_bounds__(kZtCols * kZtMaxZ, 2) zt_kernel(const __grid_c
       issue(tt + D, slot == 0 ? R - 1 : slot - 1);
       slot = slot == R - 1 ? 0 : slot + 1;
     }
-    slide(wMs, ms);
-    slide(wJs, js);
+    slide(win, make_float2(ms, js));
     if (emit) {
-      float o1 = 0.f, o2 = 0.f;
+      // K_t (M_s x) and M_t (J_s x) as the two halves of one paired FMA chain
+      float2 o = make_float2(0.f, 0.f);
       if (FAST || (y >= a.lo_t && y < a.hi_t)) {
 #pragma unroll
-        for (int w = 0; w < W; ++w) {
-          o1 = fmaf(a.iKt[w], wMs[w], o1);
-          o2 = fmaf(a.iMt[w], wJs[w], o2);
-        }
+        for (int w = 0; w < W; ++w) o = __ffma2_rn(a.iKM[w], win[w], o);
       } else {
-        o1 = chain_g(a.bKt + static_cast<size_t>(y) * a.wt, wMs);
-        o2 = chain_g(a.bMt + static_cast<size_t>(y) * a.wt, wJs);
+        const float *rK = a.bKt + static_cast<size_t>(y) * a.wt, *rM = a.bMt + static_cast<size_t>(y) * a.wt;
+#pragma unroll
+        for (int w = 0; w < W; ++w) o = __ffma2_rn(make_float2(__ldg(rK + w), __ldg(rM + w)), win[w], o);
       }
-      float out = o1 + o2;
+      float out = o.x + o.y;
       if (!FAST && y == nt - 1) out += ls;
       if (act) {
         a.y[obase + static_cast<long long>(y) * slice] = out;
@@ -1055,9 +1059,9 @@ cudaError_t launch_fused_A(const FusedA<T> &f, const T *x, T *y, cudaStream_t s)
       za.hi3 = f.hi[2];
       for (int r = 0; r < 4; ++r)
         for (int w = 0; w < 2 * f.p_s + 1; ++w) za.i3[r][w] = f.lo[2] < f.hi[2] ? f.i3[r][w] : 0.f;
+      for (int w = 0; w < 2 * f.p_s + 1; ++w) za.i3mm[w] = make_float2(za.i3[0][w], za.i3[0][w]);
       for (int w = 0; w < 2 * f.p_t + 1; ++w) {
-        za.iKt[w] = f.lo_t < f.hi_t ? f.iKt[w] : 0.f;
-        za.iMt[w] = f.lo_t < f.hi_t ? f.iMt[w] : 0.f;
+        za.iKM[w] = f.lo_t < f.hi_t ? make_float2(f.iKt[w], f.iMt[w]) : make_float2(0.f, 0.f);
       }
       return dispatch_zt(f.p_s, za, f.B, s);
     }
