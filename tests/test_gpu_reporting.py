@@ -157,3 +157,38 @@ def test_residual_history_refinement_and_batch():
     assert h0[-1] == info[0]["rel_res"]
     assert h0[-1] <= 1e-10 and np.all(np.diff(h0) < 0)
     assert list(h1) == [0.0]
+
+
+@pytest.mark.parametrize("form", [("tf32", 1), ("bf16", 2)], ids=["tf32", "bf16_batch2"])
+def test_graph_inner_loop_matches_host_loop(form):
+    """The refinement form runs each inner FP32 loop as one CUDA-graph launch
+    (while node, condition set on the device) unless phase timing is on, when
+    the host drives the loop step by step.  Both run the same kernels in the
+    same order: u, the iteration counts and the residual history must agree
+    bit for bit, and the launch counter must count the graph's kernels."""
+    prec, B = form
+    prob = STProblem(3, 3, 10)
+    S = _solver(3, 3, 10, precision=prec, refine=True, batch=B)
+    F = synth.uniform(prob.N, 31, batch=B).reshape(B, prob.N)
+    if B > 1:
+        F[1] *= 1e-3
+    Fg = _cuda(F.reshape(-1) if B == 1 else F)
+    l0 = S.launch_count()
+    u_graph, info_g = S.solve(Fg, tol=1e-10, maxit=400)
+    l_graph = S.launch_count() - l0
+    hist_g = [S.residual_history(b) for b in range(B)]
+    S.enable_timing(True)
+    l0 = S.launch_count()
+    u_host, info_h = S.solve(Fg, tol=1e-10, maxit=400)
+    l_host = S.launch_count() - l0
+    hist_h = [S.residual_history(b) for b in range(B)]
+    S.enable_timing(False)
+    assert torch.equal(u_graph, u_host)
+    for b in range(B):
+        assert info_g[b]["status"] == "ok" and info_h[b]["status"] == "ok"
+        for k in ("iters", "outer", "outer_df"):
+            assert info_g[b][k] == info_h[b][k]
+        assert info_g[b]["true_rel_res"] == info_h[b]["true_rel_res"]
+        assert np.array_equal(hist_g[b], hist_h[b])
+    # the graph adds one condition kernel per inner step
+    assert l_graph == l_host + info_g[0]["iters"]
