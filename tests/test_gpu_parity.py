@@ -205,7 +205,13 @@ def test_table1_iterations_on_gpu(n_sub, p):
 
 
 def test_square2d_p3_n64_full_size_solve():
-    """2D space + time, p = 3, 64 elements (278,850 DoF), perturbed manufactured load, tol 1e-10."""
+    """2D space + time, p = 3, 64 elements (278,850 DoF), perturbed manufactured load, tol 1e-10.
+
+    At the same CG residual (both solves stopped at 1e-10) the GPU's FP64 PCG
+    and the oracle's agree to 1e-10: the same iteration, so only rounding
+    separates them.  Against the oracle's solution to 1e-13 the tol-1e-10 solve
+    is within kappa(A) times its residual (bound 1e-8), the tol-1e-13 solve
+    within 1e-10.  The errors are printed (pytest -s)."""
     prob = STProblem(2, 3, 64)
     s = lambda x: np.sin(PI * x)
     F = prob.load_separable([(1.0, np.cos, [s, s]), (2 * PI ** 2, np.sin, [s, s])])
@@ -215,11 +221,23 @@ def test_square2d_p3_n64_full_size_solve():
     u, info = S.solve(_cuda(F), tol=1e-10, maxit=200)
     u = u.cpu().numpy()
     assert info[0]["status"] == "ok" and info[0]["true_rel_res"] <= 1e-9
-    # the oracle's own PCG with the FD preconditioner, to 1e-13
-    u_ref, it, _ = pcg(prob.apply_A_kron, FD(prob).apply, F, 1e-13, 400)
-    assert np.linalg.norm(u - u_ref) / np.linalg.norm(u_ref) <= 1e-8
+    fd = FD(prob)
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    # the oracle's own PCG with the FD preconditioner at the same tolerance
+    u_same, it_same, _ = pcg(prob.apply_A_kron, fd.apply, F, 1e-10, 400)
+    e_same = rel(u, u_same)
+    # and to 1e-13
+    u_ref, it, _ = pcg(prob.apply_A_kron, fd.apply, F, 1e-13, 400)
+    e_ref = rel(u, u_ref)
     u13, info13 = S.solve(_cuda(F), tol=1e-13, maxit=400)
-    assert np.linalg.norm(u13.cpu().numpy() - u_ref) / np.linalg.norm(u_ref) <= 1e-10
+    e13 = rel(u13.cpu().numpy(), u_ref)
+    print("\nsquare2d_p3_n64 fp64: vs oracle at the same tol 1e-10: %.2e (%d / %d it); "
+          "tol 1e-10 vs oracle 1e-13: %.2e; tol 1e-13 vs oracle 1e-13: %.2e"
+          % (e_same, info[0]["iters"], it_same, e_ref, e13))
+    assert info[0]["iters"] == it_same
+    assert e_same <= 1e-10
+    assert e_ref <= 1e-8
+    assert e13 <= 1e-10
 
 
 def test_cube3d_p3_n64_operators_sampled():
