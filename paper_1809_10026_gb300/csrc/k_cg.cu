@@ -530,10 +530,11 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSM)
   }
 }
 
-__global__ void inner_cond_kernel(const CGState *st, int B, cudaGraphConditionalHandle h) {
+__global__ void inner_cond_kernel(const CGState *st, int B, const int *err, cudaGraphConditionalHandle h) {
   unsigned go = 0;
   for (int b = 0; b < B; ++b)
     if (st[b].active && st[b].iters < st[b].limit) go = 1;
+  if (err != nullptr && *reinterpret_cast<const volatile int *>(err) != 0) go = 0;
   cudaGraphSetConditional(h, go);
 }
 
@@ -850,8 +851,9 @@ cudaError_t launch_ir_start(const double *r64, float *r32, float *d, long long N
   ir_start_kernel<<<dim3(rw.grid, B), kThreads, 0, s>>>(r64, r32, d, N, outer, inner, rw, pad, eta, limit);
   return cudaGetLastError();
 }
-cudaError_t launch_inner_cond(const CGState *st, int B, cudaGraphConditionalHandle h, cudaStream_t s) {
-  inner_cond_kernel<<<1, 1, 0, s>>>(st, B, h);
+cudaError_t launch_inner_cond(const CGState *st, int B, const int *err, cudaGraphConditionalHandle h,
+                              cudaStream_t s) {
+  inner_cond_kernel<<<1, 1, 0, s>>>(st, B, err, h);
   return cudaGetLastError();
 }
 cudaError_t launch_ir_correct(double *u, const float *d, dfloat *udf, long long N, int B, const CGState *outer,

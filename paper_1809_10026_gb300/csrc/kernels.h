@@ -197,8 +197,10 @@ cudaError_t launch_ir_start(const double *r64, float *r32, float *d, long long N
                             CGState *inner, RedWork rw, float *rpad, int n0, int np0, double eta, int limit,
                             cudaStream_t s);
 // One thread: sets the while-loop condition of a graph to "some right-hand
-// side is active with iters < limit".
-cudaError_t launch_inner_cond(const CGState *st, int B, cudaGraphConditionalHandle h, cudaStream_t s);
+// side is active with iters < limit, and no tensor-core wait has failed"
+// (err: the host-mapped failure flag of the preconditioner, or NULL).
+cudaError_t launch_inner_cond(const CGState *st, int B, const int *err, cudaGraphConditionalHandle h,
+                              cudaStream_t s);
 // u += 2^k d (k: exponent of ||r64||, as ir_start scaled); with udf != NULL
 // also writes launch_df_split's image of the new u (scale from outer).
 cudaError_t launch_ir_correct(double *u, const float *d, dfloat *udf, long long N, int B, const CGState *outer,

@@ -837,7 +837,7 @@ int inner_graph_body(stls_ctx *c, float *rpad, int pad_n0, int pad_np0, cudaGrap
   else
     STLS_LAUNCH(stls::launch_cg_xr<float>(c->di, c->ri, c->pi, c->qi, N, B, -1.0, c->st_in, c->rw, c->stream),
                 "cg_xr");
-  STLS_LAUNCH(stls::launch_inner_cond(c->st_in, B, h, c->stream), "inner_cond");
+  STLS_LAUNCH(stls::launch_inner_cond(c->st_in, B, stls::tc_fd_error_flag(c->tc), h, c->stream), "inner_cond");
   return STLS_OK;
 }
 

@@ -568,6 +568,11 @@ int tc_fd_error(const TcFd &tc) {
   return im == nullptr || im->err_host == nullptr ? 0 : *im->err_host;
 }
 
+const int *tc_fd_error_flag(const TcFd &tc) {
+  const Impl *im = static_cast<const Impl *>(tc.impl);
+  return im == nullptr ? nullptr : im->err_dev;
+}
+
 int tc_fd_launch_count(const TcFd &tc) { return tc.launches_per_apply; }
 
 float *tc_fd_padded_input(TcFd &tc, int *n0, int *np0) {

@@ -57,6 +57,9 @@ cudaError_t tc_fd_apply_f32_padded(TcFd &tc, float *z, cudaStream_t s);
 // Non-zero once a tensor-core kernel gave up on a bounded wait (host-mapped
 // flag; read it after synchronizing the stream).
 int tc_fd_error(const TcFd &tc);
+// The same flag as a device pointer (NULL without tensor-core passes), for
+// kernels that must stop work after a failed wait.
+const int *tc_fd_error_flag(const TcFd &tc);
 void tc_fd_destroy(TcFd &tc);
 
 // Fused BF16 passes (slab and streaming kernels), tc_fd_fused.cu.
