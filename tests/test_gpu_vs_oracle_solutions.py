@@ -6,7 +6,7 @@ the Kronecker-factored A of Eq. A_kron), run to a residual far below the
 solver's; its agreement with the direct solve is pinned on reduced meshes by
 the CPU suite.  Compared here:
 
-* the FP64 PCG (solved to 1e-13 where the north-star bound is 1e-10);
+* the FP64 PCG (solved to 1e-13, bound 1e-10);
 * the strict mixed forms (flexible CG with FP64 vectors and A x, tensor-core
   preconditioner with TF32 or BF16 operands) and the refinement forms
   (FP64 outer residual, FP32 inner flexible CG), solved to 1e-12, bound 1e-8;
