@@ -1009,7 +1009,9 @@ cudaError_t launch_fused_A(const FusedA<T> &f, const T *x, T *y, cudaStream_t s)
   // reads m, j', k in slices padded to 16 bytes
   int zt_Z = 0;
   if constexpr (std::is_same<T, float>::value)
-    if (f.d == 3 && f.p_t == f.p_s && f.p_s <= 4) zt_Z = zt_rows(f.n[2], f.p_s);  // higher degrees: two passes
+    // degrees 5, 6: the two passes (the fused kernel spills at two CTAs per SM and
+    // is slower than the passes at one)
+    if (f.d == 3 && f.p_t == f.p_s && f.p_s <= 4) zt_Z = zt_rows(f.n[2], f.p_s);
   const long long pitch = zt_Z > 0 ? (n1 * n2 + 3) / 4 * 4 : n1 * n2;
   sa.out_area = pitch;
   sa.n1 = f.n[0];
