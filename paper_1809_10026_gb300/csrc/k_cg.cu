@@ -200,7 +200,7 @@ struct PadIter {
 
 // (kBlocksPerSM blocks of 256 threads per SM: the reduction grid is sized for that)
 // DEFER: x += alpha p is left to the next p update (launch_cg_p with x), or to
-// launch_cg_x_pending once the loop ends; xpend records that it is owed.
+// launch_ir_correct once the loop ends; xpend records that it is owed.
 template <typename T, bool PAD = false, bool DEFER = false>
 __global__ void __launch_bounds__(kThreads, kBlocksPerSM)
     cg_xr_kernel(T *__restrict__ x, T *__restrict__ r, const T *__restrict__ p,
@@ -444,21 +444,6 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSM)
   }
 }
 
-// x += alpha p for the right-hand sides whose deferred update is still owed
-// (xpend) when the CG loop ends.
-template <typename T>
-__global__ void __launch_bounds__(kThreads, kBlocksPerSM)
-    cg_x_pending_kernel(T *__restrict__ x, const T *__restrict__ p, long long N, const CGState *st) {
-  const int b = blockIdx.y;
-  if (!st[b].xpend) return;
-  const T alpha = static_cast<T>(st[b].alpha);
-  T *xb = x + static_cast<size_t>(b) * N;
-  const T *pb = p + static_cast<size_t>(b) * N;
-  for (long long i = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x; i < N;
-       i += static_cast<long long>(gridDim.x) * kThreads)
-    xb[i] = fma(alpha, pb[i], xb[i]);
-}
-
 __global__ void __launch_bounds__(kThreads, kBlocksPerSM)
     true_residual_kernel(const double *__restrict__ F, const double *__restrict__ Ax, long long N,
                          CGState *st, RedWork rw) {
@@ -543,11 +528,15 @@ __global__ void inner_cond_kernel(const CGState *st, int B, const int *err, cuda
 // the double-float image of the new u (launch_df_split's, scaled by the
 // exponent of ||F||), for every right-hand side.
 __global__ void __launch_bounds__(kThreads, kBlocksPerSM)
-    ir_correct_kernel(double *__restrict__ u, const float *__restrict__ d, dfloat *__restrict__ udf, long long N,
-                      const CGState *outer) {
+    ir_correct_kernel(double *__restrict__ u, const float *__restrict__ d, const float *__restrict__ p,
+                      const CGState *inner, dfloat *__restrict__ udf, long long N, const CGState *outer) {
   const int b = blockIdx.y;
   const bool active = outer[b].active != 0;
   if (!active && udf == nullptr) return;
+  // the inner solve's last x += alpha p, when its CG update deferred it
+  const bool pend = active && p != nullptr && inner[b].xpend != 0;
+  const float alpha = pend ? static_cast<float>(inner[b].alpha) : 0.f;
+  const float *pb = p != nullptr ? p + static_cast<size_t>(b) * N : nullptr;
   const int k = ptx::df_scale_exp(outer[b].rr), kF = ptx::df_scale_exp(outer[b].nF2);
   double *ub = u + static_cast<size_t>(b) * N;
   const float *db = d + static_cast<size_t>(b) * N;
@@ -556,13 +545,14 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSM)
   const long long S = static_cast<long long>(gridDim.x) * kThreads;
   for (long long i = i0; i < N; i += kU * S) {
     double uv[kU];
-    float dv[kU];
+    float dv[kU], pv[kU];
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
       const long long j = i + u * S;
       if (j < N) {
         uv[u] = ub[j];
         if (active) dv[u] = db[j];
+        if (pend) pv[u] = pb[j];
       }
     }
 #pragma unroll
@@ -571,6 +561,7 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSM)
       if (j >= N) continue;
       double v = uv[u];
       if (active) {
+        if (pend) dv[u] = fmaf(alpha, pv[u], dv[u]);  // the pending update's own FP32 FMA
         v += ptx::scale_f64(ptx::f32_to_f64(dv[u]), k);
         ub[j] = v;
       }
@@ -815,10 +806,6 @@ cudaError_t launch_cg_p(const T *z, T *p, long long N, int B, int first, CGState
   cg_p_kernel<T><<<dim3(grid_1d(N), B), kThreads, 0, s>>>(z, p, N, first, st, x, tickets);
   return cudaGetLastError();
 }
-cudaError_t launch_cg_x_pending(float *x, const float *p, long long N, int B, const CGState *st, cudaStream_t s) {
-  cg_x_pending_kernel<float><<<dim3(grid_1d(N), B), kThreads, 0, s>>>(x, p, N, st);
-  return cudaGetLastError();
-}
 #define STLS_INST(T)                                                                                       \
   template cudaError_t launch_cg_alpha<T>(const T *, const T *, long long, int, CGState *, RedWork,       \
                                           cudaStream_t);                                                   \
@@ -856,9 +843,9 @@ cudaError_t launch_inner_cond(const CGState *st, int B, const int *err, cudaGrap
   inner_cond_kernel<<<1, 1, 0, s>>>(st, B, err, h);
   return cudaGetLastError();
 }
-cudaError_t launch_ir_correct(double *u, const float *d, dfloat *udf, long long N, int B, const CGState *outer,
-                              cudaStream_t s) {
-  ir_correct_kernel<<<dim3(grid_1d(N), B), kThreads, 0, s>>>(u, d, udf, N, outer);
+cudaError_t launch_ir_correct(double *u, const float *d, const float *p, const CGState *inner, dfloat *udf,
+                              long long N, int B, const CGState *outer, cudaStream_t s) {
+  ir_correct_kernel<<<dim3(grid_1d(N), B), kThreads, 0, s>>>(u, d, p, inner, udf, N, outer);
   return cudaGetLastError();
 }
 cudaError_t launch_ir_residual(const double *F, const double *Au, double *r64, long long N, int B, double tol,

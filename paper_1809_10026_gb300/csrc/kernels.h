@@ -171,7 +171,7 @@ cudaError_t launch_cg_xr(T *x, T *r, const T *p, const T *q, long long N, int B,
                          RedWork rw, cudaStream_t s);
 // cg_xr in FP32 that also writes r rounded to TF32 into rows of n0 values
 // np0 apart (per right-hand side: N / n0 rows), the TF32 preconditioner's input.
-// defer != 0: x is not updated here (see launch_cg_p).
+// defer != 0: x is not updated here (see launch_cg_p and launch_ir_correct).
 cudaError_t launch_cg_xr_pad(float *x, float *r, const float *p, const float *q, long long N, int B, double tol,
                              CGState *st, RedWork rw, float *rpad, int n0, int np0, int defer, cudaStream_t s);
 // first < 0 (launch_cg_beta, launch_cg_p): the first step of the CG loop is
@@ -185,8 +185,6 @@ cudaError_t launch_cg_beta(const T *z, const T *r, const T *q, long long N, int 
 template <typename T>
 cudaError_t launch_cg_p(const T *z, T *p, long long N, int B, int first, CGState *st, cudaStream_t s,
                         T *x = nullptr, unsigned *tickets = nullptr);
-// x += alpha p where an x update deferred by launch_cg_xr_pad is still owed.
-cudaError_t launch_cg_x_pending(float *x, const float *p, long long N, int B, const CGState *st, cudaStream_t s);
 // Refinement form: FP32 inner right-hand side r64 2^-k (||r64|| = f 2^k,
 // f in [0.5, 1)), FP64 correction of u, FP64 residual F - A u with the outer
 // convergence test.
@@ -201,10 +199,12 @@ cudaError_t launch_ir_start(const double *r64, float *r32, float *d, long long N
 // (err: the host-mapped failure flag of the preconditioner, or NULL).
 cudaError_t launch_inner_cond(const CGState *st, int B, const int *err, cudaGraphConditionalHandle h,
                               cudaStream_t s);
-// u += 2^k d (k: exponent of ||r64||, as ir_start scaled); with udf != NULL
+// u += 2^k d (k: exponent of ||r64||, as ir_start scaled); with p != NULL, d
+// first takes the x += alpha p that launch_cg_xr_pad deferred (inner[b].xpend,
+// inner[b].alpha: one FP32 FMA per entry, as the CG update would have done); with udf != NULL
 // also writes launch_df_split's image of the new u (scale from outer).
-cudaError_t launch_ir_correct(double *u, const float *d, dfloat *udf, long long N, int B, const CGState *outer,
-                              cudaStream_t s);
+cudaError_t launch_ir_correct(double *u, const float *d, const float *p, const CGState *inner, dfloat *udf,
+                              long long N, int B, const CGState *outer, cudaStream_t s);
 // `count` = 1 when the residual ends an outer step, 0 when it re-evaluates the
 // last one in FP64.
 cudaError_t launch_ir_residual(const double *F, const double *Au, double *r64, long long N, int B, double tol,

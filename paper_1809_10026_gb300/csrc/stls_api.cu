@@ -1055,11 +1055,6 @@ int solve_ir_impl(stls_ctx *c, const double *F, double *u, double tol, int maxit
         phase_end(c, ph);
       }
     }
-    if (rpad != nullptr) {  // x updates deferred by the last CG updates
-      ph = phase_begin(c, 2);
-      STLS_LAUNCH(stls::launch_cg_x_pending(c->di, c->pi, N, B, c->st_in, c->stream), "cg_x_pending");
-      phase_end(c, ph);
-    }
     if (graph) {  // the inner states after the loop, and the kernels it ran
       STLS_CK(cudaMemcpyAsync(inner_host.data(), c->st_in, sizeof(CGState) * B, cudaMemcpyDeviceToHost,
                               c->stream),
@@ -1083,7 +1078,10 @@ int solve_ir_impl(stls_ctx *c, const double *F, double *u, double tol, int maxit
     const bool use_df = c->have_df && predicted > kDfMargin * tol && predicted > kDfFloor && total_inner < maxit;
     stls::dfloat *xdf = reinterpret_cast<stls::dfloat *>(xdf_buf), *ydf = reinterpret_cast<stls::dfloat *>(q64);
     ph = phase_begin(c, 2);
-    STLS_LAUNCH(stls::launch_ir_correct(u, c->di, use_df ? xdf : nullptr, N, B, c->st, c->stream), "ir_correct");
+    // (with rpad the last CG updates deferred d += alpha p: the correction applies it)
+    STLS_LAUNCH(stls::launch_ir_correct(u, c->di, rpad != nullptr ? c->pi : nullptr, c->st_in,
+                                        use_df ? xdf : nullptr, N, B, c->st, c->stream),
+                "ir_correct");
     c->early_final = false;  // u changed since any earlier copy
     phase_end(c, ph);
     if (use_df) {  // the correction kernel wrote the double-float image of u
